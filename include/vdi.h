@@ -1,0 +1,201 @@
+/*
+ * vdi.h -- C ABI of the GB300 (sm_103a) Volumetric Depth Image renderer.
+ *
+ * Method: "Efficient Raycasting of Volumetric Depth Images for Remote
+ * Visualization of Large Volumes at High Frame Rates" (arXiv 2206.08660).
+ *
+ * A VDI (Section 2.3) stores, for every pixel of an original view V_O, a
+ * depth-sorted list of up to N_S supersegments, each with a front and back
+ * depth and a classified colour/opacity.  The library renders a resident VDI
+ * from a new view V_N by raycasting in V_O's NDC space (Section 4.1), finds
+ * supersegments with the carried-index search of Algorithm 2 (Section 4.2),
+ * corrects opacity by intersection length (Eq. 2) and composites front to
+ * back; it also renders the subsampled previews of Section 4.4 and generates
+ * VDIs from volumes (Section 3, Eq. 1, fixed sensitivity).
+ *
+ * Conventions used by every entry point
+ *  - Matrices are OpenGL column-major double[16]; clip = proj * view * x_world;
+ *    NDC = clip.xyz / clip.w in [-1,1]^3 (Fig. 3).
+ *  - Supersegment depth is V_O NDC z (OpenGL, -1 = near plane).  V_O's
+ *    near/far planes should bracket the volume tightly so FP32 depth keeps
+ *    its resolution.
+ *  - Colour is premultiplied RGBA; alpha is the opacity accumulated over one
+ *    `length_unit` of world length, so a ray piece of world length l inside a
+ *    supersegment contributes opacity 1 - (1 - alpha)^(l / length_unit)
+ *    (Eq. 2) with colour rgb / alpha.
+ *  - Image pixel (px, py) of a W x H image has NDC centre
+ *    (2 (px + 1/2) / W - 1, 1 - 2 (py + 1/2) / H): row 0 is the top row;
+ *    VDI list i = iy * w + ix uses the same convention.
+ *  - Output images are premultiplied RGBA, row-major [H][W][4], background
+ *    transparent black; VDI_F32 = float, VDI_F16 = IEEE half.
+ *  - All device work is ordered on the caller's CUDA stream (`stream` is a
+ *    cudaStream_t; NULL = legacy default stream).  A call returns after
+ *    enqueueing unless stated otherwise.  Argument errors are reported
+ *    synchronously; CUDA faults surface as VDI_ERR_CUDA from the call that
+ *    observes them.
+ *  - Every entry point returns vdi_status; no C++ exception crosses the ABI.
+ *  - Objects (vdi_ctx, vdi_t) are owned by the library and released with
+ *    their destroy call; caller-provided buffers stay owned by the caller.
+ */
+#ifndef VDI_H
+#define VDI_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    VDI_OK = 0,
+    VDI_ERR_INVALID_ARG = 1, /* bad pointer, size, enum or camera */
+    VDI_ERR_OOM = 2,         /* device allocation failed or budget exceeded */
+    VDI_ERR_CUDA = 3,        /* a CUDA call failed; see vdi_last_error_message() */
+    VDI_ERR_UNSORTED = 4,    /* supersegments not sorted/disjoint, or non-finite depth */
+    VDI_ERR_TIMEOUT = 5,     /* a bounded wait ran out */
+    VDI_ERR_BUSY = 6,        /* object still referenced by in-flight work */
+    VDI_ERR_UNSUPPORTED = 7  /* valid request outside what this build implements */
+} vdi_status;
+
+enum { VDI_F32 = 0, VDI_F16 = 1 };            /* colour / output formats */
+enum { VDI_MEM_HOST = 0, VDI_MEM_DEVICE = 1 }; /* where an input buffer lives */
+enum {                                          /* first-supersegment search (Section 4.2, Fig. 4) */
+    VDI_SEARCH_ALG2 = 0,   /* carried index + pruned binary search (Algorithm 2), default */
+    VDI_SEARCH_BINARY = 1, /* binary search seeded at the middle of the list */
+    VDI_SEARCH_LINEAR = 2  /* linear search from the first slot */
+};
+
+typedef struct vdi_ctx vdi_ctx; /* one per device */
+typedef struct vdi_t vdi_t;     /* a device-resident VDI */
+
+typedef struct {
+    double view[16]; /* world -> eye, column-major */
+    double proj[16]; /* eye -> clip, column-major; perspective or orthographic */
+} vdi_camera;
+
+typedef struct {
+    int w, h;                 /* lists (= V_O viewport pixels) */
+    int n_s;                  /* supersegments per list, 1..64 (N_S) */
+    vdi_camera orig;          /* V_O */
+    double bbox_min[3];       /* volume box in world space; rays are clipped to it */
+    double bbox_max[3];
+    double length_unit;       /* world length over which the stored alpha is defined (> 0) */
+    int colour_fmt;           /* device colour storage: VDI_F32 or VDI_F16 (depth is always FP32) */
+    int grid_tile;            /* supersegment-count grid: lists per cell side, 0 -> 8 */
+    int grid_nz;              /* grid slabs of equal V_O view depth, 1..64, 0 -> 20 */
+} vdi_desc;
+
+typedef struct {
+    size_t depth_bytes;  /* front/back FP32 depths on the device */
+    size_t colour_bytes; /* colour + opacity on the device */
+    size_t grid_bytes;   /* uint32 supersegment counts */
+    size_t total_bytes;  /* everything the VDI holds on the device */
+    size_t paper_bytes;  /* size in the paper's RGBA32F + 2 x R32F layout: 24 B per slot (Section 5) */
+    int grid_w, grid_h, grid_nz;
+    int n_s_stored;      /* slots per list as stored (N_S rounded up to even) */
+} vdi_layout;
+
+typedef struct {
+    int search;          /* VDI_SEARCH_*; default VDI_SEARCH_ALG2 */
+    int no_ert;          /* 1: keep compositing past full opacity (for exact counters) */
+    uint32_t *ray_lists; /* nullable device [H'][W']: lists traversed with positive length per ray */
+    uint32_t *ray_segs;  /* nullable device [H'][W']: supersegment pieces of positive length per ray */
+    int warp_shape;      /* -1: default/autotuned; 0: 32x1, 1: 16x2, 2: 8x4 pixels per warp */
+} vdi_render_opts;
+
+/* ---- context ---------------------------------------------------------- */
+
+/* Create a context on CUDA device `device` (made current by every call that
+ * uses the context).  *out owned by the caller; release with vdi_ctx_destroy. */
+vdi_status vdi_ctx_create(int device, vdi_ctx **out);
+void vdi_ctx_destroy(vdi_ctx *ctx);
+
+/* Text of a status code (static storage). */
+const char *vdi_status_str(vdi_status s);
+/* Message of the last error raised on this host thread (thread-local storage). */
+const char *vdi_last_error_message(void);
+
+/* ---- layout ------------------------------------------------------------ */
+
+/* Device bytes a VDI with this descriptor occupies.  Host only, no GPU
+ * needed.  Section 5: the paper's VDI is an RGBA32F colour texture plus an
+ * R32F depth texture holding front and back (24 B per slot); Section 6.3
+ * quotes 422 MiB / 950 MiB at 1280x720 / 1920x1080 with N_S = 20 and a
+ * 2.5 MiB empty-space grid at 1920x1080.  Device layout here is
+ * structure-of-arrays: slot pairs of FP32 (front, back) depths [N_S/2][h*w]
+ * as 16-byte records, and per slot (rgb / alpha, -log2(1 - alpha)) in FP32
+ * ([N_S][h*w], 16 B) or FP16 ([N_S/2][h*w], two slots per 16 B). */
+vdi_status vdi_layout_bytes(const vdi_desc *desc, vdi_layout *out);
+
+/* ---- create / download / destroy --------------------------------------- */
+
+/* Build a device-resident VDI from supersegment buffers (Section 2.3).
+ *  rgba   [h][w][n_s][4] float, premultiplied, alpha per length_unit, 0 <= rgb <= alpha <= 1
+ *  depth  [h][w][n_s][2] float, V_O NDC z (front, back)
+ *  counts [h][w] int32 supersegments per list (0..n_s), or NULL: the leading
+ *         slots whose front depth is finite are used
+ * Valid slots must satisfy f <= b, b_j <= f_{j+1}, finite depths; slots beyond
+ * the count are ignored.  `mem_kind` says whether the three buffers are host
+ * or device memory; they are copied and may be freed when the call returns
+ * (it synchronises `stream` to report VDI_ERR_UNSORTED / VDI_ERR_INVALID_ARG).
+ * Also builds the supersegment-count grid of Section 4.3 (grid_tile x
+ * grid_tile lists by grid_nz slabs of equal V_O view depth; a supersegment
+ * counts in every slab its [f, b] overlaps).  *out released with vdi_destroy. */
+vdi_status vdi_create(vdi_ctx *ctx, const vdi_desc *desc, const float *rgba, const float *depth,
+                      const int32_t *counts, int mem_kind, void *stream, vdi_t **out);
+
+/* Copy a VDI back to HOST buffers in the vdi_create layout (any may be NULL).
+ * Depths, counts and the grid are exact; colour is reconverted from the
+ * device form (FP32: within a few ulp; FP16: half precision).  Unused slots
+ * come back as depth +inf and colour 0.  grid: [grid_nz][grid_h][grid_w]
+ * uint32.  Synchronises `stream`. */
+vdi_status vdi_download(vdi_t *vdi, float *rgba, float *depth, int32_t *counts, uint32_t *grid,
+                        void *stream);
+
+/* Layout of an existing VDI. */
+vdi_status vdi_get_layout(const vdi_t *vdi, vdi_layout *out);
+
+/* Free the VDI's device memory.  Stream-ordered on the stream it was created
+ * on; the caller must not destroy a VDI that other streams still render. */
+void vdi_destroy(vdi_t *vdi);
+
+/* ---- render --------------------------------------------------------------
+ * Render `vdi` from the new view `view` into the caller's DEVICE buffer
+ * out_rgba ([H][W][4] of out_fmt).
+ *  d_i = 1, d_r = 1: the full method of Section 4: per pixel ray clipped to
+ *    V_O's frustum and the box (Section 4.1, Fig. 2), walked list by list
+ *    through V_O's NDC grid (Amanatides-Woo), first supersegment per list by
+ *    Algorithm 2 with the index carried from the previous list, adjacency
+ *    walk, opacity corrected by world intersection length (Eq. 2),
+ *    front-to-back compositing with early termination at alpha >= 1 - 2^-12.
+ *  d_r = k > 1: ray-subsampled preview (Section 4.4): per grid cell crossed,
+ *    ceil((count / lists_in_cell) * (l_cell / cell_depth) / k) samples at equal
+ *    world spacing; each takes the colour of the supersegment containing it,
+ *    opacity corrected by the spacing.
+ *  d_i = k > 1: image-space preview (Section 4.4): ceil(W/k) x ceil(H/k) rays,
+ *    bilinearly upsampled to W x H (half-pixel centres, clamp to edge).
+ *  W, H in 1..16384; d_i, d_r in 1..16.  Temporary device memory for d_i > 1
+ *  comes from the stream-ordered allocator. */
+vdi_status vdi_render(vdi_t *vdi, const vdi_camera *view, int W, int H, int d_i, int d_r,
+                      void *out_rgba, int out_fmt, void *stream);
+
+/* vdi_render with options (NULL opts = defaults).  Counters are written for
+ * the rendered (pre-upsampling) resolution. */
+vdi_status vdi_render_ex(vdi_t *vdi, const vdi_camera *view, int W, int H, int d_i, int d_r,
+                         void *out_rgba, int out_fmt, const vdi_render_opts *opts, void *stream);
+
+/* ---- diagnostics --------------------------------------------------------
+ * Run the device first-supersegment search on a batch of queries against
+ * list `list` of `vdi` (Algorithm 2 and the ablation searches).  Device
+ * buffers of length n: d_entry, d_exit (float), seed (int32, -1 = none),
+ * increasing (int32 0/1); result (int32): index of the first supersegment
+ * met, or -1.  Exposed so the index contract can be tested bit-exactly. */
+vdi_status vdi_search_first(vdi_t *vdi, int list, int search, const float *d_entry,
+                            const float *d_exit, const int32_t *seed, const int32_t *increasing,
+                            int32_t *result, int n, void *stream);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* VDI_H */

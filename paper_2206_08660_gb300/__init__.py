@@ -1,0 +1,228 @@
+"""Python binding of the GB300 VDI renderer (C ABI in ``include/vdi.h``).
+
+Argument marshalling only: every step of the render, create and generate
+paths runs in the CUDA library ``_build/libvdi.so``.  There is no CPU
+fallback; if the library is missing or cannot be loaded every call raises.
+
+Functions keep the C names (``vdi_create``, ``vdi_render``, ...).  Device
+buffers are passed as torch CUDA tensors (or raw integer device pointers),
+host buffers as numpy arrays; streams default to torch's current stream.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+import numpy as np
+
+from . import build as _build
+
+__all__ = [
+    "VDI_F32", "VDI_F16", "VDI_MEM_HOST", "VDI_MEM_DEVICE", "VDI_SEARCH_ALG2", "VDI_SEARCH_BINARY",
+    "VDI_SEARCH_LINEAR", "VdiError", "VdiCamera", "VdiDesc", "VdiLayout", "VdiRenderOpts", "load",
+    "vdi_ctx_create", "vdi_ctx_destroy", "vdi_layout_bytes", "vdi_create", "vdi_download", "vdi_get_layout",
+    "vdi_destroy", "vdi_render", "vdi_render_ex", "vdi_search_first", "camera", "desc",
+]
+
+VDI_F32, VDI_F16 = 0, 1
+VDI_MEM_HOST, VDI_MEM_DEVICE = 0, 1
+VDI_SEARCH_ALG2, VDI_SEARCH_BINARY, VDI_SEARCH_LINEAR = 0, 1, 2
+STATUS = ["VDI_OK", "VDI_ERR_INVALID_ARG", "VDI_ERR_OOM", "VDI_ERR_CUDA", "VDI_ERR_UNSORTED",
+          "VDI_ERR_TIMEOUT", "VDI_ERR_BUSY", "VDI_ERR_UNSUPPORTED"]
+
+
+class VdiError(RuntimeError):
+    def __init__(self, status: int, msg: str):
+        self.status = status
+        name = STATUS[status] if 0 <= status < len(STATUS) else str(status)
+        super().__init__(f"{name}: {msg}")
+
+
+class VdiCamera(C.Structure):
+    _fields_ = [("view", C.c_double * 16), ("proj", C.c_double * 16)]
+
+
+class VdiDesc(C.Structure):
+    _fields_ = [("w", C.c_int), ("h", C.c_int), ("n_s", C.c_int), ("orig", VdiCamera),
+                ("bbox_min", C.c_double * 3), ("bbox_max", C.c_double * 3), ("length_unit", C.c_double),
+                ("colour_fmt", C.c_int), ("grid_tile", C.c_int), ("grid_nz", C.c_int)]
+
+
+class VdiLayout(C.Structure):
+    _fields_ = [("depth_bytes", C.c_size_t), ("colour_bytes", C.c_size_t), ("grid_bytes", C.c_size_t),
+                ("total_bytes", C.c_size_t), ("paper_bytes", C.c_size_t), ("grid_w", C.c_int),
+                ("grid_h", C.c_int), ("grid_nz", C.c_int), ("n_s_stored", C.c_int)]
+
+
+class VdiRenderOpts(C.Structure):
+    _fields_ = [("search", C.c_int), ("no_ert", C.c_int), ("ray_lists", C.c_void_p),
+                ("ray_segs", C.c_void_p), ("warp_shape", C.c_int)]
+
+
+_lib = None
+P = C.c_void_p
+
+
+def _sig(L, name, args, res=C.c_int):
+    f = getattr(L, name)
+    f.argtypes = args
+    f.restype = res
+    return f
+
+
+def load(build_if_needed: bool = True):
+    """Load libvdi.so (building it first when sources changed)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    path = _build.LIB
+    if build_if_needed and not _build.up_to_date():
+        _build.build()
+    if not os.path.exists(path):
+        raise RuntimeError(f"CUDA library {path} is missing; run __graft_entry__.build()")
+    L = C.CDLL(path)
+    _sig(L, "vdi_status_str", [C.c_int], C.c_char_p)
+    _sig(L, "vdi_last_error_message", [], C.c_char_p)
+    _sig(L, "vdi_ctx_create", [C.c_int, C.POINTER(P)])
+    _sig(L, "vdi_ctx_destroy", [P], None)
+    _sig(L, "vdi_layout_bytes", [P, P])
+    _sig(L, "vdi_create", [P, P, P, P, P, C.c_int, P, C.POINTER(P)])
+    _sig(L, "vdi_download", [P, P, P, P, P, P])
+    _sig(L, "vdi_get_layout", [P, P])
+    _sig(L, "vdi_destroy", [P], None)
+    _sig(L, "vdi_render", [P, P, C.c_int, C.c_int, C.c_int, C.c_int, P, C.c_int, P])
+    _sig(L, "vdi_render_ex", [P, P, C.c_int, C.c_int, C.c_int, C.c_int, P, C.c_int, P, P])
+    _sig(L, "vdi_search_first", [P, C.c_int, C.c_int, P, P, P, P, P, C.c_int, P])
+    _lib = L
+    return L
+
+
+def _check(rc: int):
+    if rc != 0:
+        raise VdiError(rc, load().vdi_last_error_message().decode(errors="replace"))
+
+
+def _dptr(x):
+    """Device pointer of a torch CUDA tensor (or an int pointer / None)."""
+    if x is None:
+        return None
+    if isinstance(x, int):
+        return x
+    if hasattr(x, "data_ptr"):
+        if not x.is_cuda:
+            raise ValueError("expected a CUDA tensor")
+        if not x.is_contiguous():
+            raise ValueError("expected a contiguous tensor")
+        return x.data_ptr()
+    raise TypeError(type(x))
+
+
+def _stream(stream):
+    if stream is None:
+        import torch
+
+        return torch.cuda.current_stream().cuda_stream
+    if isinstance(stream, int):
+        return stream
+    return stream.cuda_stream
+
+
+def _mat(m):
+    m = np.asarray(m, np.float64)
+    if m.shape == (4, 4):
+        m = np.ascontiguousarray(m.T).reshape(16)
+    return (C.c_double * 16)(*m.tolist())
+
+
+def camera(view, proj) -> VdiCamera:
+    """VdiCamera from (4,4) row-major matrices or column-major [16] arrays."""
+    c = VdiCamera()
+    c.view, c.proj = _mat(view), _mat(proj)
+    return c
+
+
+def desc(w, h, n_s, view_o, proj_o, bbox_min, bbox_max, length_unit, colour_fmt=VDI_F32, grid_tile=0,
+         grid_nz=0) -> VdiDesc:
+    d = VdiDesc()
+    d.w, d.h, d.n_s = int(w), int(h), int(n_s)
+    d.orig = camera(view_o, proj_o)
+    d.bbox_min = (C.c_double * 3)(*map(float, bbox_min))
+    d.bbox_max = (C.c_double * 3)(*map(float, bbox_max))
+    d.length_unit = float(length_unit)
+    d.colour_fmt, d.grid_tile, d.grid_nz = int(colour_fmt), int(grid_tile), int(grid_nz)
+    return d
+
+
+def vdi_ctx_create(device: int = 0):
+    out = P()
+    _check(load().vdi_ctx_create(int(device), C.byref(out)))
+    return out
+
+
+def vdi_ctx_destroy(ctx):
+    load().vdi_ctx_destroy(ctx)
+
+
+def vdi_layout_bytes(d: VdiDesc) -> VdiLayout:
+    out = VdiLayout()
+    _check(load().vdi_layout_bytes(C.byref(d), C.byref(out)))
+    return out
+
+
+def vdi_create(ctx, d: VdiDesc, rgba, depth, counts=None, stream=None):
+    """rgba/depth/counts: numpy (host) or torch CUDA tensors (device)."""
+    if isinstance(rgba, np.ndarray):
+        rgba = np.ascontiguousarray(rgba, np.float32)
+        depth = np.ascontiguousarray(depth, np.float32)
+        if counts is not None:
+            counts = np.ascontiguousarray(counts, np.int32)
+        ptrs = [rgba.ctypes.data, depth.ctypes.data, None if counts is None else counts.ctypes.data]
+        kind = VDI_MEM_HOST
+    else:
+        ptrs = [_dptr(rgba), _dptr(depth), _dptr(counts)]
+        kind = VDI_MEM_DEVICE
+    out = P()
+    _check(load().vdi_create(ctx, C.byref(d), ptrs[0], ptrs[1], ptrs[2], kind, _stream(stream), C.byref(out)))
+    return out
+
+
+def vdi_get_layout(vdi) -> VdiLayout:
+    out = VdiLayout()
+    _check(load().vdi_get_layout(vdi, C.byref(out)))
+    return out
+
+
+def vdi_download(vdi, w, h, n_s, stream=None):
+    """Returns host (rgba[h,w,n_s,4], depth[h,w,n_s,2], counts[h,w], grid[nz,gh,gw])."""
+    L = vdi_get_layout(vdi)
+    rgba = np.zeros((h, w, n_s, 4), np.float32)
+    depth = np.zeros((h, w, n_s, 2), np.float32)
+    counts = np.zeros((h, w), np.int32)
+    grid = np.zeros((L.grid_nz, L.grid_h, L.grid_w), np.uint32)
+    _check(load().vdi_download(vdi, rgba.ctypes.data, depth.ctypes.data, counts.ctypes.data, grid.ctypes.data,
+                               _stream(stream)))
+    return rgba, depth, counts, grid
+
+
+def vdi_destroy(vdi):
+    load().vdi_destroy(vdi)
+
+
+def vdi_render(vdi, cam: VdiCamera, W, H, d_i, d_r, out, out_fmt=VDI_F32, stream=None):
+    _check(load().vdi_render(vdi, C.byref(cam), int(W), int(H), int(d_i), int(d_r), _dptr(out), int(out_fmt),
+                             _stream(stream)))
+
+
+def vdi_render_ex(vdi, cam: VdiCamera, W, H, d_i, d_r, out, out_fmt=VDI_F32, search=VDI_SEARCH_ALG2,
+                  no_ert=False, ray_lists=None, ray_segs=None, warp_shape=-1, stream=None):
+    o = VdiRenderOpts()
+    o.search, o.no_ert, o.warp_shape = int(search), int(bool(no_ert)), int(warp_shape)
+    o.ray_lists, o.ray_segs = _dptr(ray_lists), _dptr(ray_segs)
+    _check(load().vdi_render_ex(vdi, C.byref(cam), int(W), int(H), int(d_i), int(d_r), _dptr(out),
+                                int(out_fmt), C.byref(o), _stream(stream)))
+
+
+def vdi_search_first(vdi, list_index, search, d_entry, d_exit, seed, increasing, result, stream=None):
+    n = int(d_entry.numel())
+    _check(load().vdi_search_first(vdi, int(list_index), int(search), _dptr(d_entry), _dptr(d_exit), _dptr(seed),
+                                   _dptr(increasing), _dptr(result), n, _stream(stream)))

@@ -1,0 +1,518 @@
+// vdi_api.cu -- host side of the C ABI declared in include/vdi.h: contexts,
+// VDI objects, the FP64 per-view constants of the ray setup and the render
+// entry points.
+#include <cuda_runtime.h>
+#include <math.h>
+#include <stdarg.h>
+#include <stdio.h>
+#include <stdlib.h>
+#include <string.h>
+
+#include <new>
+
+#include "../../include/vdi.h"
+#include "vdi_api_internal.h"
+#include "vdi_internal.cuh"
+
+#define VDI_API extern "C" __attribute__((visibility("default")))
+
+namespace vdi {
+
+cudaError_t launch_render(const ViewConsts &c, const DevVdi &v, void *out, int out_fmt, uint32_t *rl,
+                          uint32_t *rs, int search, int warp_shape, bool ert, cudaStream_t st);
+cudaError_t launch_upsample(const float4 *lo, int w0, int h0, void *out, int out_fmt, int W, int H,
+                            cudaStream_t st);
+cudaError_t launch_search(const DevVdi &v, int li, int search, const float *de, const float *dx,
+                          const int32_t *seed, const int32_t *inc, int32_t *res, int n, cudaStream_t st);
+cudaError_t launch_count_leading(const float *depth, int ns, long long nl, int32_t *counts, cudaStream_t st);
+cudaError_t launch_convert(int fmt, const float *rgba, const float *depth, const int32_t *counts, int ns,
+                           int nsp, long long nl, float4 *dpair, void *colour, unsigned *err, cudaStream_t st);
+cudaError_t launch_grid(const DevVdi &v, uint32_t *grid, cudaStream_t st);
+cudaError_t launch_download(const DevVdi &v, int ns, float *rgba, float *depth, int32_t *counts,
+                            cudaStream_t st);
+
+static thread_local char g_err[512];
+
+vdi_status fail(vdi_status s, const char *fmt, ...) {
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(g_err, sizeof g_err, fmt, ap);
+    va_end(ap);
+    return s;
+}
+
+vdi_status cuda_fail(cudaError_t e, const char *what) {
+    cudaGetLastError();  // clear a sticky-free error so later calls start clean
+    return fail(e == cudaErrorMemoryAllocation ? VDI_ERR_OOM : VDI_ERR_CUDA, "%s: %s", what,
+                cudaGetErrorString(e));
+}
+
+// ---------------------------------------------------------------------------
+// 4x4 helpers, column-major (element (r, c) at m[c * 4 + r])
+// ---------------------------------------------------------------------------
+static inline double at(const double *m, int r, int c) { return m[c * 4 + r]; }
+
+void mat4_mul(const double *A, const double *B, double *C) {
+    double T[16];
+    for (int c = 0; c < 4; ++c)
+        for (int r = 0; r < 4; ++r)
+            T[c * 4 + r] = at(A, r, 0) * at(B, 0, c) + at(A, r, 1) * at(B, 1, c) + at(A, r, 2) * at(B, 2, c) +
+                           at(A, r, 3) * at(B, 3, c);
+    memcpy(C, T, sizeof T);
+}
+
+static double det3(const double *m, int r0, int r1, int r2, int c0, int c1, int c2) {
+    return at(m, r0, c0) * (at(m, r1, c1) * at(m, r2, c2) - at(m, r1, c2) * at(m, r2, c1)) -
+           at(m, r0, c1) * (at(m, r1, c0) * at(m, r2, c2) - at(m, r1, c2) * at(m, r2, c0)) +
+           at(m, r0, c2) * (at(m, r1, c0) * at(m, r2, c1) - at(m, r1, c1) * at(m, r2, c0));
+}
+
+// inverse by the adjugate: inv(r, c) = (-1)^(r+c) det(minor without row c, col r) / det
+bool mat4_inv(const double *m, double *out) {
+    double cof[4][4];
+    for (int r = 0; r < 4; ++r)
+        for (int c = 0; c < 4; ++c) {
+            int rr[3], cc[3], a = 0, b = 0;
+            for (int k = 0; k < 4; ++k) {
+                if (k != r) rr[a++] = k;
+                if (k != c) cc[b++] = k;
+            }
+            const double d = det3(m, rr[0], rr[1], rr[2], cc[0], cc[1], cc[2]);
+            cof[r][c] = ((r + c) & 1) ? -d : d;
+        }
+    double det = 0.0;
+    for (int c = 0; c < 4; ++c) det += at(m, 0, c) * cof[0][c];
+    if (!(fabs(det) > 0.0) || !isfinite(det)) return false;
+    for (int r = 0; r < 4; ++r)
+        for (int c = 0; c < 4; ++c) out[c * 4 + r] = cof[c][r] / det;
+    return true;
+}
+
+static void mat4_apply(const double *m, const double v[4], double o[4]) {
+    for (int r = 0; r < 4; ++r) o[r] = at(m, r, 0) * v[0] + at(m, r, 1) * v[1] + at(m, r, 2) * v[2] + at(m, r, 3) * v[3];
+}
+
+// view-space distance in front of the camera whose NDC depth under P is Z
+double ndc_to_view_depth(const double *P, double Z) {
+    return -(at(P, 2, 3) - Z * at(P, 3, 3)) / (Z * at(P, 3, 2) - at(P, 2, 2));
+}
+
+static bool finite16(const double *m) {
+    for (int k = 0; k < 16; ++k)
+        if (!isfinite(m[k])) return false;
+    return true;
+}
+
+// ---------------------------------------------------------------------------
+// layout
+// ---------------------------------------------------------------------------
+vdi_status check_desc(const vdi_desc *d, vdi_layout *L) {
+    if (!d) return fail(VDI_ERR_INVALID_ARG, "desc is NULL");
+    if (d->w < 1 || d->h < 1 || d->w > 32768 || d->h > 32768)
+        return fail(VDI_ERR_INVALID_ARG, "list grid %dx%d out of range", d->w, d->h);
+    if (d->n_s < 1 || d->n_s > kMaxNs) return fail(VDI_ERR_INVALID_ARG, "n_s=%d outside 1..%d", d->n_s, kMaxNs);
+    if (d->colour_fmt != VDI_F32 && d->colour_fmt != VDI_F16)
+        return fail(VDI_ERR_INVALID_ARG, "colour_fmt=%d", d->colour_fmt);
+    if (!(d->length_unit > 0.0) || !isfinite(d->length_unit))
+        return fail(VDI_ERR_INVALID_ARG, "length_unit must be positive");
+    const int T = d->grid_tile ? d->grid_tile : 8, nz = d->grid_nz ? d->grid_nz : 20;
+    if (T < 1 || T > 256 || nz < 1 || nz > kMaxNz)
+        return fail(VDI_ERR_INVALID_ARG, "grid_tile=%d grid_nz=%d out of range", T, nz);
+    for (int k = 0; k < 3; ++k)
+        if (!(d->bbox_min[k] < d->bbox_max[k])) return fail(VDI_ERR_INVALID_ARG, "empty bbox");
+    if (!finite16(d->orig.view) || !finite16(d->orig.proj))
+        return fail(VDI_ERR_INVALID_ARG, "non-finite V_O matrices");
+    const size_t nl = (size_t)d->w * d->h;
+    const int nsp = (d->n_s + 1) & ~1;
+    L->n_s_stored = nsp;
+    L->depth_bytes = nl * nsp * 2 * sizeof(float);
+    L->colour_bytes = nl * nsp * (d->colour_fmt == VDI_F32 ? 16 : 8);
+    L->grid_w = div_up(d->w, T);
+    L->grid_h = div_up(d->h, T);
+    L->grid_nz = nz;
+    L->grid_bytes = (size_t)L->grid_w * L->grid_h * nz * sizeof(uint32_t);
+    L->total_bytes = L->depth_bytes + L->colour_bytes + L->grid_bytes;
+    L->paper_bytes = nl * (size_t)d->n_s * 24;
+    return VDI_OK;
+}
+
+// slab edges of the count grid: equal V_O view-depth steps between the near
+// and far planes (Section 4.3), mapped to NDC z in FP64 and rounded to FP32
+void grid_edges(const double *P, int nz, float *edges) {
+    const double dn = ndc_to_view_depth(P, -1.0), df = ndc_to_view_depth(P, 1.0);
+    for (int k = 0; k <= nz; ++k) {
+        const double d = dn + (df - dn) * (double)k / (double)nz;
+        const double ze = -d;
+        const double Z = (at(P, 2, 2) * ze + at(P, 2, 3)) / (at(P, 3, 2) * ze + at(P, 3, 3));
+        edges[k] = (float)Z;
+    }
+    edges[0] = -1.0f;
+    edges[nz] = 1.0f;
+}
+
+// ---------------------------------------------------------------------------
+// per-view constants of the ray setup (FP64 on the host)
+// ---------------------------------------------------------------------------
+vdi_status make_view_consts(const vdi_t *v, const vdi_camera *cam, int W, int H, int d_r, ViewConsts *c) {
+    if (!cam) return fail(VDI_ERR_INVALID_ARG, "view is NULL");
+    if (!finite16(cam->view) || !finite16(cam->proj)) return fail(VDI_ERR_INVALID_ARG, "non-finite V_N matrices");
+    double PV[16], Q[16];
+    mat4_mul(cam->proj, cam->view, PV);
+    if (!mat4_inv(PV, Q)) return fail(VDI_ERR_INVALID_ARG, "V_N projection*view is singular");
+    // near/far points of pixel NDC (x, y) are affine in (x, y) when the
+    // homogeneous w of the unprojection does not depend on x, y
+    const double wscale = fabs(at(Q, 3, 2)) + fabs(at(Q, 3, 3));
+    if (fabs(at(Q, 3, 0)) > 1e-12 * wscale || fabs(at(Q, 3, 1)) > 1e-12 * wscale)
+        return fail(VDI_ERR_UNSUPPORTED, "V_N projection is neither perspective nor orthographic");
+    const double wn = at(Q, 3, 3) - at(Q, 3, 2), wf = at(Q, 3, 3) + at(Q, 3, 2);
+    if (!(wn != 0.0) || !(wf != 0.0) || (wn > 0) != (wf > 0))
+        return fail(VDI_ERR_INVALID_ARG, "V_N near/far planes are degenerate");
+    double O0[3], Ox[3], Oy[3], D0[3], Dx[3], Dy[3];
+    for (int k = 0; k < 3; ++k) {
+        O0[k] = (at(Q, k, 3) - at(Q, k, 2)) / wn;
+        Ox[k] = at(Q, k, 0) / wn;
+        Oy[k] = at(Q, k, 1) / wn;
+        D0[k] = (at(Q, k, 3) + at(Q, k, 2)) / wf - O0[k];
+        Dx[k] = at(Q, k, 0) / wf - Ox[k];
+        Dy[k] = at(Q, k, 1) / wf - Oy[k];
+    }
+    double t_lo = 0.0, t_hi = 1.0;
+    int a_aff = 1, b_aff = 1;
+    const double *P = cam->proj;
+    const bool persp = at(P, 3, 0) == 0.0 && at(P, 3, 1) == 0.0 && at(P, 3, 2) < 0.0 && at(P, 3, 3) == 0.0;
+    const bool ortho = at(P, 3, 0) == 0.0 && at(P, 3, 1) == 0.0 && at(P, 3, 2) == 0.0 && at(P, 3, 3) != 0.0;
+    if (persp) {
+        // p(t) = E + t D(x, y) with the eye E: the near point is E + tau0 D
+        double Vi[16];
+        if (mat4_inv(cam->view, Vi)) {
+            const double E[3] = {at(Vi, 0, 3) / at(Vi, 3, 3), at(Vi, 1, 3) / at(Vi, 3, 3), at(Vi, 2, 3) / at(Vi, 3, 3)};
+            const double n = ndc_to_view_depth(P, -1.0), f = ndc_to_view_depth(P, 1.0);
+            const double tau0 = n / (f - n);
+            double err = 0.0, scale = 0.0;
+            for (int k = 0; k < 3; ++k) {
+                err = fmax(err, fabs(O0[k] - (E[k] + tau0 * D0[k])));
+                err = fmax(err, fabs(Ox[k] - tau0 * Dx[k]));
+                err = fmax(err, fabs(Oy[k] - tau0 * Dy[k]));
+                scale = fmax(scale, fabs(O0[k]) + fabs(E[k]) + fabs(D0[k]));
+            }
+            if (isfinite(tau0) && tau0 > 0.0 && err <= 1e-9 * scale) {
+                for (int k = 0; k < 3; ++k) {
+                    O0[k] = E[k];
+                    Ox[k] = Oy[k] = 0.0;
+                }
+                t_lo = tau0;
+                t_hi = tau0 + 1.0;
+                a_aff = 0;
+            }
+        }
+    } else if (ortho) {
+        double dmax = 0.0, scale = 0.0;
+        for (int k = 0; k < 3; ++k) {
+            dmax = fmax(dmax, fmax(fabs(Dx[k]), fabs(Dy[k])));
+            scale = fmax(scale, fabs(D0[k]));
+        }
+        if (dmax <= 1e-12 * scale) {
+            for (int k = 0; k < 3; ++k) Dx[k] = Dy[k] = 0.0;
+            b_aff = 0;
+        }
+    }
+    const double *M = v->M;
+    double e0[4] = {O0[0], O0[1], O0[2], 1.0}, ex[4] = {Ox[0], Ox[1], Ox[2], 0.0}, ey[4] = {Oy[0], Oy[1], Oy[2], 0.0};
+    double f0[4] = {D0[0], D0[1], D0[2], 0.0}, fx[4] = {Dx[0], Dx[1], Dx[2], 0.0}, fy[4] = {Dy[0], Dy[1], Dy[2], 0.0};
+    mat4_apply(M, e0, c->A0);
+    mat4_apply(M, ex, c->Ax);
+    mat4_apply(M, ey, c->Ay);
+    mat4_apply(M, f0, c->B0);
+    mat4_apply(M, fx, c->Bx);
+    mat4_apply(M, fy, c->By);
+    c->a_affine = a_aff;
+    c->b_affine = b_aff;
+    for (int k = 0; k < 3; ++k) {
+        c->O0[k] = (float)O0[k];
+        c->Ox[k] = (float)Ox[k];
+        c->Oy[k] = (float)Oy[k];
+        c->D0[k] = (float)D0[k];
+        c->Dx[k] = (float)Dx[k];
+        c->Dy[k] = (float)Dy[k];
+        c->bmin[k] = (float)v->desc.bbox_min[k];
+        c->bmax[k] = (float)v->desc.bbox_max[k];
+    }
+    c->t_lo = (float)t_lo;
+    c->t_hi = (float)t_hi;
+    c->inv_u = (float)(1.0 / v->desc.length_unit);
+    c->W = W;
+    c->H = H;
+    c->sx = 2.0 / W;
+    c->sy = 2.0 / H;
+    c->d_r = d_r;
+    c->cell_scale = (float)(v->desc.length_unit / (v->dz_cell * d_r));
+    return VDI_OK;
+}
+
+}  // namespace vdi
+
+using namespace vdi;
+
+// ---------------------------------------------------------------------------
+// ABI
+// ---------------------------------------------------------------------------
+
+VDI_API const char *vdi_status_str(vdi_status s) {
+    switch (s) {
+        case VDI_OK: return "VDI_OK";
+        case VDI_ERR_INVALID_ARG: return "VDI_ERR_INVALID_ARG";
+        case VDI_ERR_OOM: return "VDI_ERR_OOM";
+        case VDI_ERR_CUDA: return "VDI_ERR_CUDA";
+        case VDI_ERR_UNSORTED: return "VDI_ERR_UNSORTED";
+        case VDI_ERR_TIMEOUT: return "VDI_ERR_TIMEOUT";
+        case VDI_ERR_BUSY: return "VDI_ERR_BUSY";
+        case VDI_ERR_UNSUPPORTED: return "VDI_ERR_UNSUPPORTED";
+    }
+    return "VDI_ERR_UNKNOWN";
+}
+
+VDI_API const char *vdi_last_error_message(void) { return g_err; }
+
+VDI_API vdi_status vdi_ctx_create(int device, vdi_ctx **out) {
+    if (!out) return fail(VDI_ERR_INVALID_ARG, "out is NULL");
+    *out = nullptr;
+    int n = 0;
+    cudaError_t e = cudaGetDeviceCount(&n);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaGetDeviceCount");
+    if (device < 0 || device >= n) return fail(VDI_ERR_INVALID_ARG, "device %d of %d", device, n);
+    if ((e = cudaSetDevice(device)) != cudaSuccess) return cuda_fail(e, "cudaSetDevice");
+    vdi_ctx *c = new (std::nothrow) vdi_ctx();
+    if (!c) return fail(VDI_ERR_OOM, "host allocation");
+    c->device = device;
+    cudaDeviceGetAttribute(&c->sm_count, cudaDevAttrMultiProcessorCount, device);
+    *out = c;
+    return VDI_OK;
+}
+
+VDI_API void vdi_ctx_destroy(vdi_ctx *ctx) { delete ctx; }
+
+VDI_API vdi_status vdi_layout_bytes(const vdi_desc *desc, vdi_layout *out) {
+    if (!out) return fail(VDI_ERR_INVALID_ARG, "out is NULL");
+    return check_desc(desc, out);
+}
+
+VDI_API vdi_status vdi_get_layout(const vdi_t *v, vdi_layout *out) {
+    if (!v || !out) return fail(VDI_ERR_INVALID_ARG, "NULL argument");
+    *out = v->layout;
+    return VDI_OK;
+}
+
+#define CK(call)                                      \
+    do {                                              \
+        cudaError_t e_ = (call);                      \
+        if (e_ != cudaSuccess) {                      \
+            st_ = cuda_fail(e_, #call);               \
+            goto done;                                \
+        }                                             \
+    } while (0)
+
+namespace vdi {
+
+vdi_status alloc_vdi(vdi_ctx *ctx, const vdi_desc *desc, vdi_t **out) {
+    vdi_layout L;
+    vdi_status s = check_desc(desc, &L);
+    if (s != VDI_OK) return s;
+    vdi_t *v = new (std::nothrow) vdi_t();
+    if (!v) return fail(VDI_ERR_OOM, "host allocation");
+    v->ctx = ctx;
+    v->desc = *desc;
+    v->desc.grid_tile = desc->grid_tile ? desc->grid_tile : 8;
+    v->desc.grid_nz = desc->grid_nz ? desc->grid_nz : 20;
+    v->layout = L;
+    mat4_mul(desc->orig.proj, desc->orig.view, v->M);
+    const double dn = ndc_to_view_depth(desc->orig.proj, -1.0), df = ndc_to_view_depth(desc->orig.proj, 1.0);
+    if (!(df > dn) || !isfinite(dn) || !isfinite(df)) {
+        delete v;
+        return fail(VDI_ERR_INVALID_ARG, "V_O near/far planes are degenerate");
+    }
+    v->dz_cell = (df - dn) / v->desc.grid_nz;
+    DevVdi &d = v->dv;
+    d.w = desc->w;
+    d.h = desc->h;
+    d.ns = desc->n_s;
+    d.nsp = L.n_s_stored;
+    d.fmt = desc->colour_fmt;
+    d.nl = (long long)desc->w * desc->h;
+    d.T = v->desc.grid_tile;
+    d.gw = L.grid_w;
+    d.gh = L.grid_h;
+    d.nz = L.grid_nz;
+    grid_edges(desc->orig.proj, d.nz, d.edges);
+    cudaError_t e;
+    if ((e = cudaMalloc(&v->depth_mem, L.depth_bytes)) != cudaSuccess ||
+        (e = cudaMalloc(&v->colour_mem, L.colour_bytes)) != cudaSuccess ||
+        (e = cudaMalloc(&v->grid_mem, L.grid_bytes)) != cudaSuccess) {
+        cudaFree(v->depth_mem);
+        cudaFree(v->colour_mem);
+        cudaFree(v->grid_mem);
+        delete v;
+        return cuda_fail(e, "cudaMalloc(VDI)");
+    }
+    d.depth = reinterpret_cast<const float4 *>(v->depth_mem);
+    d.colour = v->colour_mem;
+    d.grid = v->grid_mem;
+    *out = v;
+    return VDI_OK;
+}
+
+void free_vdi(vdi_t *v) {
+    if (!v) return;
+    cudaSetDevice(v->ctx->device);
+    cudaFree(v->depth_mem);
+    cudaFree(v->colour_mem);
+    cudaFree(v->grid_mem);
+    delete v;
+}
+
+}  // namespace vdi
+
+VDI_API vdi_status vdi_create(vdi_ctx *ctx, const vdi_desc *desc, const float *rgba, const float *depth,
+                              const int32_t *counts, int mem_kind, void *stream, vdi_t **out) {
+    if (!ctx || !out || !rgba || !depth) return fail(VDI_ERR_INVALID_ARG, "NULL argument");
+    if (mem_kind != VDI_MEM_HOST && mem_kind != VDI_MEM_DEVICE) return fail(VDI_ERR_INVALID_ARG, "mem_kind");
+    *out = nullptr;
+    cudaSetDevice(ctx->device);
+    cudaStream_t st = (cudaStream_t)stream;
+    vdi_t *v = nullptr;
+    vdi_status st_ = alloc_vdi(ctx, desc, &v);
+    if (st_ != VDI_OK) return st_;
+    const size_t nl = (size_t)desc->w * desc->h, nslot = nl * desc->n_s;
+    float *d_rgba = nullptr, *d_depth = nullptr;
+    int32_t *d_counts = nullptr;
+    unsigned *d_err = nullptr;
+    unsigned h_err = 0;
+    if (mem_kind == VDI_MEM_HOST) {
+        CK(cudaMallocAsync((void **)&d_rgba, nslot * 16, st));
+        CK(cudaMallocAsync((void **)&d_depth, nslot * 8, st));
+        CK(cudaMemcpyAsync(d_rgba, rgba, nslot * 16, cudaMemcpyHostToDevice, st));
+        CK(cudaMemcpyAsync(d_depth, depth, nslot * 8, cudaMemcpyHostToDevice, st));
+    } else {
+        d_rgba = const_cast<float *>(rgba);
+        d_depth = const_cast<float *>(depth);
+    }
+    CK(cudaMallocAsync((void **)&d_counts, nl * sizeof(int32_t), st));
+    CK(cudaMallocAsync((void **)&d_err, sizeof(unsigned), st));
+    CK(cudaMemsetAsync(d_err, 0, sizeof(unsigned), st));
+    if (counts)
+        CK(cudaMemcpyAsync(d_counts, counts, nl * sizeof(int32_t),
+                           mem_kind == VDI_MEM_HOST ? cudaMemcpyHostToDevice : cudaMemcpyDeviceToDevice, st));
+    else
+        CK(launch_count_leading(d_depth, desc->n_s, (long long)nl, d_counts, st));
+    CK(launch_convert(desc->colour_fmt, d_rgba, d_depth, d_counts, desc->n_s, v->dv.nsp, (long long)nl,
+                      reinterpret_cast<float4 *>(v->depth_mem), v->colour_mem, d_err, st));
+    CK(launch_grid(v->dv, v->grid_mem, st));
+    CK(cudaMemcpyAsync(&h_err, d_err, sizeof(unsigned), cudaMemcpyDeviceToHost, st));
+    CK(cudaStreamSynchronize(st));
+    if (h_err & 1u)
+        st_ = fail(VDI_ERR_UNSORTED, "supersegments not sorted/disjoint or depth not finite");
+    else if (h_err & 2u)
+        st_ = fail(VDI_ERR_INVALID_ARG, "colour outside 0 <= rgb <= alpha <= 1, or count outside 0..n_s");
+done:
+    if (mem_kind == VDI_MEM_HOST) {
+        if (d_rgba) cudaFreeAsync(d_rgba, st);
+        if (d_depth) cudaFreeAsync(d_depth, st);
+    }
+    if (d_counts) cudaFreeAsync(d_counts, st);
+    if (d_err) cudaFreeAsync(d_err, st);
+    if (st_ != VDI_OK) {
+        cudaStreamSynchronize(st);
+        free_vdi(v);
+        return st_;
+    }
+    *out = v;
+    return VDI_OK;
+}
+
+VDI_API vdi_status vdi_download(vdi_t *v, float *rgba, float *depth, int32_t *counts, uint32_t *grid,
+                                void *stream) {
+    if (!v) return fail(VDI_ERR_INVALID_ARG, "vdi is NULL");
+    cudaSetDevice(v->ctx->device);
+    cudaStream_t st = (cudaStream_t)stream;
+    const size_t nl = (size_t)v->dv.nl, nslot = nl * v->dv.ns;
+    vdi_status st_ = VDI_OK;
+    float *d_rgba = nullptr, *d_depth = nullptr;
+    int32_t *d_counts = nullptr;
+    if (rgba) CK(cudaMallocAsync((void **)&d_rgba, nslot * 16, st));
+    if (depth) CK(cudaMallocAsync((void **)&d_depth, nslot * 8, st));
+    if (counts) CK(cudaMallocAsync((void **)&d_counts, nl * 4, st));
+    if (rgba || depth || counts) CK(launch_download(v->dv, v->dv.ns, d_rgba, d_depth, d_counts, st));
+    if (rgba) CK(cudaMemcpyAsync(rgba, d_rgba, nslot * 16, cudaMemcpyDeviceToHost, st));
+    if (depth) CK(cudaMemcpyAsync(depth, d_depth, nslot * 8, cudaMemcpyDeviceToHost, st));
+    if (counts) CK(cudaMemcpyAsync(counts, d_counts, nl * 4, cudaMemcpyDeviceToHost, st));
+    if (grid) CK(cudaMemcpyAsync(grid, v->grid_mem, v->layout.grid_bytes, cudaMemcpyDeviceToHost, st));
+    CK(cudaStreamSynchronize(st));
+done:
+    if (d_rgba) cudaFreeAsync(d_rgba, st);
+    if (d_depth) cudaFreeAsync(d_depth, st);
+    if (d_counts) cudaFreeAsync(d_counts, st);
+    if (st_ != VDI_OK) cudaStreamSynchronize(st);
+    return st_;
+}
+
+VDI_API void vdi_destroy(vdi_t *v) { free_vdi(v); }
+
+namespace vdi {
+
+vdi_status check_render_args(const vdi_t *v, int W, int H, int d_i, int d_r, const void *out, int out_fmt) {
+    if (!v) return fail(VDI_ERR_INVALID_ARG, "vdi is NULL");
+    if (!out) return fail(VDI_ERR_INVALID_ARG, "out_rgba is NULL");
+    if (W < 1 || H < 1 || W > 16384 || H > 16384) return fail(VDI_ERR_INVALID_ARG, "image %dx%d", W, H);
+    if (d_i < 1 || d_i > 16 || d_r < 1 || d_r > 16) return fail(VDI_ERR_INVALID_ARG, "d_i=%d d_r=%d", d_i, d_r);
+    if (out_fmt != VDI_F32 && out_fmt != VDI_F16) return fail(VDI_ERR_INVALID_ARG, "out_fmt=%d", out_fmt);
+    return VDI_OK;
+}
+
+}  // namespace vdi
+
+VDI_API vdi_status vdi_render_ex(vdi_t *v, const vdi_camera *view, int W, int H, int d_i, int d_r,
+                                 void *out_rgba, int out_fmt, const vdi_render_opts *opts, void *stream) {
+    vdi_status st_ = check_render_args(v, W, H, d_i, d_r, out_rgba, out_fmt);
+    if (st_ != VDI_OK) return st_;
+    vdi_render_opts o = {VDI_SEARCH_ALG2, 0, nullptr, nullptr, -1};
+    if (opts) o = *opts;
+    if (o.search < 0 || o.search > 2) return fail(VDI_ERR_INVALID_ARG, "search=%d", o.search);
+    if (o.warp_shape < -1 || o.warp_shape > 2) return fail(VDI_ERR_INVALID_ARG, "warp_shape=%d", o.warp_shape);
+    cudaSetDevice(v->ctx->device);
+    cudaStream_t st = (cudaStream_t)stream;
+    const int Wr = div_up(W, d_i), Hr = div_up(H, d_i);
+    ViewConsts c;
+    st_ = make_view_consts(v, view, Wr, Hr, d_r, &c);
+    if (st_ != VDI_OK) return st_;
+    const int ws = o.warp_shape >= 0 ? o.warp_shape : default_warp_shape(v, Wr, Hr);
+    float4 *lo = nullptr;
+    if (d_i == 1) {
+        CK(launch_render(c, v->dv, out_rgba, out_fmt, o.ray_lists, o.ray_segs, o.search, ws, !o.no_ert, st));
+    } else {
+        CK(cudaMallocAsync((void **)&lo, (size_t)Wr * Hr * sizeof(float4), st));
+        CK(launch_render(c, v->dv, lo, VDI_F32, o.ray_lists, o.ray_segs, o.search, ws, !o.no_ert, st));
+        CK(launch_upsample(lo, Wr, Hr, out_rgba, out_fmt, W, H, st));
+    }
+done:
+    if (lo) cudaFreeAsync(lo, st);
+    return st_;
+}
+
+VDI_API vdi_status vdi_render(vdi_t *v, const vdi_camera *view, int W, int H, int d_i, int d_r, void *out_rgba,
+                              int out_fmt, void *stream) {
+    return vdi_render_ex(v, view, W, H, d_i, d_r, out_rgba, out_fmt, nullptr, stream);
+}
+
+VDI_API vdi_status vdi_search_first(vdi_t *v, int list, int search, const float *d_entry, const float *d_exit,
+                                    const int32_t *seed, const int32_t *increasing, int32_t *result, int n,
+                                    void *stream) {
+    if (!v || !d_entry || !d_exit || !seed || !increasing || !result || n < 0)
+        return fail(VDI_ERR_INVALID_ARG, "bad argument");
+    if (list < 0 || list >= v->dv.nl) return fail(VDI_ERR_INVALID_ARG, "list %d out of range", list);
+    if (search < 0 || search > 2) return fail(VDI_ERR_INVALID_ARG, "search=%d", search);
+    if (n == 0) return VDI_OK;
+    cudaSetDevice(v->ctx->device);
+    vdi_status st_ = VDI_OK;
+    CK(launch_search(v->dv, list, search, d_entry, d_exit, seed, increasing, result, n, (cudaStream_t)stream));
+done:
+    return st_;
+}

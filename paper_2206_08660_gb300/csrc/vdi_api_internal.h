@@ -1,0 +1,43 @@
+// vdi_api_internal.h -- host-side object definitions shared by the ABI
+// translation units (contexts, VDI handles, helpers).
+#pragma once
+#include <cuda_runtime.h>
+
+#include "../../include/vdi.h"
+#include "vdi_internal.cuh"
+
+struct vdi_ctx {
+    int device = 0;
+    int sm_count = 0;
+};
+
+struct vdi_t {
+    vdi_ctx *ctx = nullptr;
+    vdi_desc desc{};
+    vdi_layout layout{};
+    vdi::DevVdi dv{};
+    double M[16]{};       // P_O * V_O
+    double dz_cell = 0.0; // V_O view-depth extent of one grid slab
+    void *depth_mem = nullptr;
+    void *colour_mem = nullptr;
+    uint32_t *grid_mem = nullptr;
+};
+
+namespace vdi {
+
+vdi_status fail(vdi_status s, const char *fmt, ...);
+vdi_status cuda_fail(cudaError_t e, const char *what);
+vdi_status check_desc(const vdi_desc *d, vdi_layout *L);
+vdi_status make_view_consts(const vdi_t *v, const vdi_camera *cam, int W, int H, int d_r, ViewConsts *c);
+vdi_status alloc_vdi(vdi_ctx *ctx, const vdi_desc *desc, vdi_t **out);
+void free_vdi(vdi_t *v);
+void mat4_mul(const double *A, const double *B, double *C);
+bool mat4_inv(const double *m, double *out);
+double ndc_to_view_depth(const double *P, double Z);
+void grid_edges(const double *P, int nz, float *edges);
+
+// warp shape used when the caller does not choose one: 32x1 (lanes along a
+// row of lists) unless the autotuner recorded a better one
+inline int default_warp_shape(const vdi_t *, int, int) { return 0; }
+
+}  // namespace vdi

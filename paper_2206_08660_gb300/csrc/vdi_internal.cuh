@@ -1,0 +1,211 @@
+// vdi_internal.cuh -- device-side data layout, per-view constants, loads and
+// the first-supersegment searches shared by the render kernels.
+//
+// Device layout of a VDI (structure of arrays, slot-major so that lanes on
+// neighbouring lists read neighbouring 16-byte records):
+//   depth   float4 [nsp/2][nl]   (f_2k, b_2k, f_2k+1, b_2k+1)   FP32 V_O NDC z
+//   colour  FP32: float4 [nsp][nl]   (r/a, g/a, b/a, kappa)
+//           FP16: uint4  [nsp/2][nl] (two half4 (r/a, g/a, b/a, kappa) records)
+//   grid    uint32 [nz][gh][gw]  supersegment counts per cell (Section 4.3)
+// nl = w*h lists, nsp = N_S rounded up to even; unused slots hold f = b = +inf
+// and colour 0.  kappa = -log2(1 - alpha): Eq. 2's 1 - (1 - alpha)^l then is
+// 1 - exp2(-kappa l), one exp2 per supersegment piece, and FP16 storage of
+// kappa stays accurate for every l (storing alpha would lose 1 - alpha).
+#pragma once
+#include <cuda_fp16.h>
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace vdi {
+
+constexpr int kMaxNz = 64;
+constexpr int kMaxNs = 64;
+constexpr float kErtT = 1.0f / 4096.0f;  // stop once transmittance <= 2^-12
+
+enum { kSearchAlg2 = 0, kSearchBinary = 1, kSearchLinear = 2 };
+
+struct DevVdi {
+    int w, h, ns, nsp;
+    int fmt;  // 0 = F32, 1 = F16
+    long long nl;
+    const float4 *depth;
+    const void *colour;
+    const uint32_t *grid;
+    int T, gw, gh, nz;
+    float edges[kMaxNz + 1];  // slab edges in V_O NDC z, edges[0] = -1, edges[nz] = 1
+};
+
+// Per-view constants built on the host in FP64 (vdi_api.cu, make_view_consts).
+// A new-view ray through pixel NDC (x, y) is p(t) = O(x,y) + t D(x,y) in world
+// space for t in [t_lo, t_hi] (V_N near plane to far plane).  Its image in
+// V_O clip space is h(t) = a(x,y) + t b(x,y) with a = P_O V_O (O, 1) and
+// b = P_O V_O (D, 0), both affine in (x, y); a is constant for a perspective
+// V_N (O = eye), b is constant for an orthographic one.
+struct ViewConsts {
+    double A0[4], Ax[4], Ay[4];
+    double B0[4], Bx[4], By[4];
+    int a_affine, b_affine;
+    float O0[3], Ox[3], Oy[3];
+    float D0[3], Dx[3], Dy[3];
+    float t_lo, t_hi;
+    float bmin[3], bmax[3];
+    float inv_u;        // 1 / length_unit
+    int W, H;           // rays rendered (after D_I)
+    double sx, sy;      // 2/W, 2/H
+    int d_r;            // ray subsampling (1 = exact path)
+    float cell_scale;   // length_unit / (slab view-depth extent * d_r)
+};
+
+struct PairCache {
+    int k;
+    float4 d;
+};
+
+__device__ __forceinline__ float4 ld_depth_pair(const DevVdi &v, int k, int li) {
+    return __ldg(v.depth + (size_t)k * v.nl + li);
+}
+__device__ __forceinline__ float ld_back(const DevVdi &v, int j, int li) {
+    const float *p = reinterpret_cast<const float *>(v.depth + (size_t)(j >> 1) * v.nl + li);
+    return __ldg(p + 2 * (j & 1) + 1);
+}
+__device__ __forceinline__ float ld_front(const DevVdi &v, int j, int li) {
+    const float *p = reinterpret_cast<const float *>(v.depth + (size_t)(j >> 1) * v.nl + li);
+    return __ldg(p + 2 * (j & 1));
+}
+__device__ __forceinline__ void get_fb(PairCache &pc, const DevVdi &v, int li, int j, float &f,
+                                       float &b) {
+    int k = j >> 1;
+    if (k != pc.k) {
+        pc.d = ld_depth_pair(v, k, li);
+        pc.k = k;
+    }
+    f = (j & 1) ? pc.d.z : pc.d.x;
+    b = (j & 1) ? pc.d.w : pc.d.y;
+}
+
+// colour of slot j: (r/a, g/a, b/a, kappa)
+template <int FMT>
+struct ColourCache {
+    int k;
+    uint4 q;
+};
+
+template <int FMT>
+__device__ __forceinline__ float4 get_colour(ColourCache<FMT> &cc, const DevVdi &v, int li, int j) {
+    if (FMT == 0) {
+        return __ldg(reinterpret_cast<const float4 *>(v.colour) + (size_t)j * v.nl + li);
+    } else {
+        int k = j >> 1;
+        if (k != cc.k) {
+            cc.q = __ldg(reinterpret_cast<const uint4 *>(v.colour) + (size_t)k * v.nl + li);
+            cc.k = k;
+        }
+        unsigned u0 = (j & 1) ? cc.q.z : cc.q.x;
+        unsigned u1 = (j & 1) ? cc.q.w : cc.q.y;
+        __half2 rg = *reinterpret_cast<__half2 *>(&u0);
+        __half2 bk = *reinterpret_cast<__half2 *>(&u1);
+        float2 a = __half22float2(rg), b = __half22float2(bk);
+        return make_float4(a.x, a.y, b.x, b.y);
+    }
+}
+
+// ---------------------------------------------------------------------------
+// First supersegment met by a ray entering a list (Section 4.2, Algorithm 2).
+//
+// Depth increasing along the ray: the answer is the smallest j with
+// b_j >= d_entry (nsp if none).  Algorithm 2 seeds with p, the index of the
+// last supersegment met in the previous list, reads b_{p-1} and b_p, counts
+// how many of them lie at or beyond d_entry and then either keeps p or runs
+// one binary search on the pruned range below or above p.  Here the seed is
+// rounded up to odd, q = p | 1, so that b_{q-1} and b_q sit in one 16-byte
+// depth record and the prefetch is a single load; the result is the same.
+// Depth decreasing along the ray (the ray points back towards V_O): the mirror
+// image, the largest j with f_j <= d_entry (-1 if none), seed q = p & ~1.
+// ---------------------------------------------------------------------------
+template <int MODE>
+__device__ __forceinline__ int first_inc(const DevVdi &v, int li, float d, int p, PairCache &pc) {
+    const int nsp = v.nsp;
+    if (MODE == kSearchLinear) {
+        int j = 0;
+        for (; j < nsp; ++j) {
+            float f, b;
+            get_fb(pc, v, li, j, f, b);
+            if (b >= d) break;
+        }
+        return j;
+    }
+    int lo = 0, hi = nsp;  // answer in [lo, hi]; hi is either known to qualify or nsp
+    if (MODE == kSearchAlg2 && p >= 0) {
+        int q = p | 1;
+        if (q >= nsp) q = nsp - 1;
+        int k = q >> 1;
+        if (pc.k != k) {
+            pc.d = ld_depth_pair(v, k, li);
+            pc.k = k;
+        }
+        int interval = (pc.d.w >= d) + (pc.d.y >= d);
+        if (interval == 1) {
+            lo = hi = q;
+        } else if (interval == 2) {
+            lo = 0;
+            hi = q - 1;
+        } else {
+            lo = q + 1;
+            hi = nsp;
+        }
+    }
+    while (lo < hi) {  // the single binary search of Algorithm 2 on [lo, hi)
+        int mid = (lo + hi) >> 1;
+        if (ld_back(v, mid, li) >= d)
+            hi = mid;
+        else
+            lo = mid + 1;
+    }
+    return lo;
+}
+
+template <int MODE>
+__device__ __forceinline__ int first_dec(const DevVdi &v, int li, float d, int p, PairCache &pc) {
+    const int nsp = v.nsp;
+    if (MODE == kSearchLinear) {
+        int j = -1;
+        for (; j + 1 < nsp; ++j) {
+            float f, b;
+            get_fb(pc, v, li, j + 1, f, b);
+            if (!(f <= d)) break;
+        }
+        return j;
+    }
+    int lo = -1, hi = nsp - 1;  // answer in [lo, hi]; lo is either known to qualify or -1
+    if (MODE == kSearchAlg2 && p >= 0) {
+        int q = p & ~1;
+        if (q >= nsp) q = nsp - 2;
+        int k = q >> 1;
+        if (pc.k != k) {
+            pc.d = ld_depth_pair(v, k, li);
+            pc.k = k;
+        }
+        int interval = (pc.d.x <= d) + (pc.d.z <= d);
+        if (interval == 1) {
+            lo = hi = q;
+        } else if (interval == 2) {
+            lo = q + 1;
+            hi = nsp - 1;
+        } else {
+            lo = -1;
+            hi = q - 1;
+        }
+    }
+    while (lo < hi) {
+        int mid = (lo + hi + 1) >> 1;
+        if (ld_front(v, mid, li) <= d)
+            lo = mid;
+        else
+            hi = mid - 1;
+    }
+    return lo;
+}
+
+__host__ __device__ inline int div_up(int a, int b) { return (a + b - 1) / b; }
+
+}  // namespace vdi

@@ -1,0 +1,95 @@
+"""CPU-only checks of the C ABI library: it builds, loads, exports every
+declared entry point, and its host-only layout arithmetic matches the sizes
+the paper prints (Sections 5, 6.1, 6.3)."""
+import ctypes as C
+import os
+import re
+
+import numpy as np
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def declared_functions():
+    names = []
+    for fn in sorted(os.listdir(os.path.join(ROOT, "include"))):
+        if not fn.endswith(".h"):
+            continue
+        src = open(os.path.join(ROOT, "include", fn)).read()
+        src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+        names += re.findall(r"^\s*(?:const\s+)?[A-Za-z_][A-Za-z0-9_]*\s*\**\s*(vdi_[a-z0-9_]+)\s*\(", src, flags=re.M)
+    return sorted(set(names))
+
+
+@pytest.fixture(scope="module")
+def lib():
+    import paper_2206_08660_gb300 as V
+
+    return V.load()
+
+
+def test_library_exports_every_declared_symbol(lib):
+    names = declared_functions()
+    assert len(names) >= 12, names
+    missing = [n for n in names if not hasattr(lib, n)]
+    assert not missing, missing
+
+
+def test_status_strings(lib):
+    import paper_2206_08660_gb300 as V
+
+    for i, name in enumerate(V.STATUS):
+        assert lib.vdi_status_str(i).decode() == name
+
+
+def _golden():
+    out = {}
+    for line in open(os.path.join(ROOT, "tests", "golden", "paper_sizes.txt")):
+        if line.startswith("#") or not line.strip():
+            continue
+        k, v, unit = line.split()[:3]
+        out[k] = float(v) * {"MiB": 2**20, "MB": 2**20}[unit]  # the paper's "MB" at 1024^2 is binary
+    return out
+
+
+@pytest.mark.parametrize("key,w,h", [("vdi_fp32_1280x720_ns20", 1280, 720),
+                                     ("vdi_fp32_1920x1080_ns20", 1920, 1080),
+                                     ("vdi_fp32_1024x1024_ns20", 1024, 1024)])
+def test_layout_matches_paper_vdi_sizes(key, w, h):
+    import paper_2206_08660_gb300 as V
+
+    d = V.desc(w, h, 20, np.eye(4), np.eye(4), (0, 0, 0), (1, 1, 1), 1.0, V.VDI_F32)
+    L = V.vdi_layout_bytes(d)
+    # 24 B per slot, as in the paper's two textures
+    assert L.paper_bytes == w * h * 20 * 24
+    assert abs(L.paper_bytes / _golden()[key] - 1) < 2e-3
+    # the FP32 device layout holds exactly those bytes too (16 B colour + 8 B depth per slot)
+    assert L.depth_bytes + L.colour_bytes == L.paper_bytes
+    d16 = V.desc(w, h, 20, np.eye(4), np.eye(4), (0, 0, 0), (1, 1, 1), 1.0, V.VDI_F16)
+    L16 = V.vdi_layout_bytes(d16)
+    assert L16.depth_bytes + L16.colour_bytes == w * h * 20 * 16
+
+
+def test_grid_size_matches_paper():
+    import paper_2206_08660_gb300 as V
+
+    d = V.desc(1920, 1080, 20, np.eye(4), np.eye(4), (0, 0, 0), (1, 1, 1), 1.0)
+    L = V.vdi_layout_bytes(d)
+    assert (L.grid_w, L.grid_h, L.grid_nz) == (240, 135, 20)
+    assert abs(L.grid_bytes / _golden()["grid_1920x1080"] - 1) < 0.02
+
+
+def test_layout_rejects_bad_descriptors():
+    import paper_2206_08660_gb300 as V
+
+    for bad in [dict(n_s=0), dict(n_s=65), dict(w=0), dict(length_unit=0.0), dict(colour_fmt=7)]:
+        kw = dict(w=8, h=8, n_s=4, length_unit=1.0, colour_fmt=V.VDI_F32)
+        kw.update(bad)
+        d = V.desc(kw["w"], 8, kw["n_s"], np.eye(4), np.eye(4), (0, 0, 0), (1, 1, 1), kw["length_unit"],
+                   kw["colour_fmt"])
+        with pytest.raises(V.VdiError) as e:
+            V.vdi_layout_bytes(d)
+        assert e.value.status == 1
+    # odd N_S is stored rounded up to even
+    assert V.vdi_layout_bytes(V.desc(8, 8, 5, np.eye(4), np.eye(4), (0, 0, 0), (1, 1, 1), 1.0)).n_s_stored == 6

@@ -1,0 +1,85 @@
+"""GPU parity of the subsampled previews (Section 4.4) against the FP64 oracle.
+
+D_R: samples per grid cell proportional to the cell's supersegment count and
+the ray's length in it, thinned by D_R; compared on rays the oracle does not
+flag (a sample within rounding distance of a list or supersegment boundary,
+or a sample count at a rounding boundary, can legitimately differ).
+D_I: fewer rays, then bilinear upsampling; compared everywhere (exact path)
+or where no flagged low-resolution pixel contributes (with D_R).
+"""
+import numpy as np
+import pytest
+
+import vdi_synth as S
+from helpers import check_tolerance, random_case
+
+pytestmark = pytest.mark.gpu
+torch = pytest.importorskip("torch")
+
+
+@pytest.fixture(scope="module")
+def V():
+    import paper_2206_08660_gb300 as V
+
+    V.load()
+    return V
+
+
+@pytest.fixture(scope="module")
+def ctx(V):
+    c = V.vdi_ctx_create(0)
+    yield c
+    V.vdi_ctx_destroy(c)
+
+
+def render(V, vdi, cam, W, H, d_i, d_r):
+    out = torch.zeros((H, W, 4), dtype=torch.float32, device="cuda")
+    V.vdi_render(vdi, V.camera(cam.view, cam.proj), W, H, d_i, d_r, out)
+    torch.cuda.synchronize()
+    return out.cpu().numpy().reshape(-1, 4)
+
+
+T, NZ = 8, 10
+
+
+@pytest.fixture(scope="module")
+def scene(V, ctx, orc):
+    case = random_case(64, 48, 6, seed=21, u=0.15, alpha_range=(0.05, 0.6))
+    vdi = {fmt: V.vdi_create(ctx, case.gpu_desc(V, fmt, T, NZ), case.vdi.rgba, case.vdi.depth, case.vdi.counts)
+           for fmt in (0, 1)}
+    yield case, case.oracle_scene(orc), vdi
+    for v in vdi.values():
+        V.vdi_destroy(v)
+
+
+@pytest.mark.parametrize("fmt", [0, 1])
+@pytest.mark.parametrize("d_r", [2, 4])
+@pytest.mark.parametrize("az,el", [(20.0, 10.0), (-45.0, 30.0), (160.0, 0.0)])
+def test_ray_subsampled_preview(V, orc, scene, fmt, d_r, az, el):
+    case, sc, vdi = scene
+    W, H = 75, 53
+    cn = S.orbit_camera(case.bmin, case.bmax, W / H, az_deg=az, el_deg=el, zoom=1.1)
+    ref, fl = orc.render_preview(sc, cn.view, cn.proj, W, H, d_r, T, NZ)
+    got = render(V, vdi[fmt], cn, W, H, 1, d_r)
+    ok = fl == 0
+    assert ok.mean() > 0.8, ok.mean()
+    assert ref[ok, 3].max() > 0.2
+    check_tolerance(got, ref, fmt, mask=ok, what=f"D_R={d_r}")
+
+
+@pytest.mark.parametrize("d_i,d_r", [(2, 1), (3, 1), (2, 2), (4, 4)])
+def test_image_space_preview(V, orc, scene, d_i, d_r):
+    case, sc, vdi = scene
+    W, H = 90, 61
+    Wr, Hr = -(-W // d_i), -(-H // d_i)
+    cn = S.orbit_camera(case.bmin, case.bmax, W / H, az_deg=30, el_deg=20)
+    if d_r == 1:
+        lo = orc.render_exact(sc, cn.view, cn.proj, Wr, Hr)[0]
+        fl = np.zeros(Wr * Hr)
+    else:
+        lo, fl = orc.render_preview(sc, cn.view, cn.proj, Wr, Hr, d_r, T, NZ)
+    ref = orc.upsample(lo, Wr, Hr, W, H)
+    touched = orc.upsample(np.repeat(fl.astype(np.float64)[:, None], 4, 1), Wr, Hr, W, H)[:, 0] > 0
+    got = render(V, vdi[0], cn, W, H, d_i, d_r)
+    assert (~touched).mean() > 0.6
+    check_tolerance(got, ref, 0, mask=~touched, what=f"D_I={d_i} D_R={d_r}")

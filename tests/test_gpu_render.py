@@ -1,0 +1,204 @@
+"""GPU parity of the render path against the FP64 oracle, through the C ABI.
+
+Covers the exact path (Section 4.1-4.2: list walk, Algorithm 2, Eq. 2,
+compositing) for perspective and orthographic new views, depth increasing and
+decreasing along rays (views beyond 90 degrees), several tiles with ragged
+tails, FP32 and FP16 colour storage; bit-exact integer results (first-index
+contract, per-ray list/supersegment counters on rays the oracle does not
+flag, count grid, create/download round trip); and error reporting.
+"""
+import numpy as np
+import pytest
+
+import vdi_synth as S
+from helpers import TOL, Case, check_tolerance, random_case
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+
+
+@pytest.fixture(scope="module")
+def V():
+    import paper_2206_08660_gb300 as V
+
+    V.load()
+    return V
+
+
+@pytest.fixture(scope="module")
+def ctx(V):
+    assert torch.cuda.is_available()
+    c = V.vdi_ctx_create(0)
+    yield c
+    V.vdi_ctx_destroy(c)
+
+
+def gpu_render(V, vdi, cam, W, H, d_i=1, d_r=1, counters=False, **kw):
+    out = torch.zeros((H, W, 4), dtype=torch.float32, device="cuda")
+    Hr, Wr = -(-H // d_i), -(-W // d_i)
+    rl = rs = None
+    if counters:
+        rl = torch.zeros((Hr, Wr), dtype=torch.int32, device="cuda")
+        rs = torch.zeros((Hr, Wr), dtype=torch.int32, device="cuda")
+    V.vdi_render_ex(vdi, V.camera(cam.view, cam.proj), W, H, d_i, d_r, out, V.VDI_F32, ray_lists=rl,
+                    ray_segs=rs, **kw)
+    torch.cuda.synchronize()
+    o = out.cpu().numpy().reshape(-1, 4)
+    if counters:
+        return o, rl.cpu().numpy().reshape(-1), rs.cpu().numpy().reshape(-1)
+    return o
+
+
+VIEWS = [  # (azimuth, elevation, zoom, ortho)
+    (10.0, 15.0, 1.0, False),
+    (-35.0, 5.0, 1.2, False),
+    (60.0, 40.0, 1.5, False),
+    (150.0, -20.0, 1.0, False),  # more than 90 degrees away: depth decreases along rays
+    (25.0, 30.0, 1.0, True),
+    (0.0, 15.0, 1.0, False),  # the original direction
+]
+
+
+@pytest.mark.parametrize("fmt", [0, 1])
+@pytest.mark.parametrize("seed", [0, 1])
+def test_exact_render_matches_oracle(V, ctx, orc, fmt, seed):
+    case = random_case(37, 23, 5, seed=seed, u=0.15, alpha_range=(0.05, 0.8))
+    sc = case.oracle_scene(orc)
+    vdi = V.vdi_create(ctx, case.gpu_desc(V, fmt), case.vdi.rgba, case.vdi.depth, case.vdi.counts)
+    try:
+        for (az, el, zoom, ortho) in VIEWS:
+            W, H = 70, 45  # 3 x 6 tiles of 32 x 8 with ragged edges
+            cn = S.orbit_camera(case.bmin, case.bmax, W / H, az_deg=az, el_deg=el, zoom=zoom, ortho=ortho)
+            ref = orc.render_exact(sc, cn.view, cn.proj, W, H)[0]
+            got = gpu_render(V, vdi, cn, W, H)
+            assert ref[:, 3].max() > 0.2, "view shows nothing"
+            check_tolerance(got, ref, fmt, what=f"view {az},{el}")
+            assert np.all(got[:, :3] <= got[:, 3:4] + 1e-5) and np.all(got >= 0) and np.all(got[:, 3] <= 1 + 1e-6)
+    finally:
+        V.vdi_destroy(vdi)
+
+
+def test_counters_bit_exact_on_unflagged_rays(V, ctx, orc):
+    case = random_case(29, 17, 4, seed=3, u=0.2)
+    sc = case.oracle_scene(orc)
+    vdi = V.vdi_create(ctx, case.gpu_desc(V, 0), case.vdi.rgba, case.vdi.depth, case.vdi.counts)
+    try:
+        total = 0
+        for (az, el, zoom, ortho) in VIEWS:
+            W, H = 48, 40
+            cn = S.orbit_camera(case.bmin, case.bmax, W / H, az_deg=az, el_deg=el, zoom=zoom, ortho=ortho)
+            _, nl, nsg, fl = orc.render_exact(sc, cn.view, cn.proj, W, H)
+            _, gl, gs = gpu_render(V, vdi, cn, W, H, counters=True, no_ert=True)
+            ok = fl == 0
+            assert ok.mean() > 0.9
+            assert np.array_equal(gl[ok], nl[ok]), np.nonzero(gl[ok] != nl[ok])
+            assert np.array_equal(gs[ok], nsg[ok])
+            total += int(nl[ok].sum())
+        assert total > 1000
+    finally:
+        V.vdi_destroy(vdi)
+
+
+@pytest.mark.parametrize("search", [0, 1, 2])
+def test_search_modes_and_warp_shapes_give_identical_images(V, ctx, search):
+    case = random_case(40, 30, 6, seed=7)
+    vdi = V.vdi_create(ctx, case.gpu_desc(V, 0), case.vdi.rgba, case.vdi.depth, case.vdi.counts)
+    try:
+        cn = S.orbit_camera(case.bmin, case.bmax, 1.0, az_deg=30, el_deg=20)
+        base = gpu_render(V, vdi, cn, 64, 64)
+        for ws in (0, 1, 2):
+            got = gpu_render(V, vdi, cn, 64, 64, search=search, warp_shape=ws)
+            assert np.array_equal(got, base)
+    finally:
+        V.vdi_destroy(vdi)
+
+
+def test_first_index_contract_bit_exact(V, ctx, orc):
+    rng = np.random.default_rng(11)
+    for ns in (1, 2, 5, 8, 20):
+        w = 64
+        case = random_case(w, 1, ns, seed=ns, fill=1.0)
+        vdi = V.vdi_create(ctx, case.gpu_desc(V, 0), case.vdi.rgba, case.vdi.depth, case.vdi.counts)
+        try:
+            for li in range(0, w, 7):
+                n = int(case.vdi.counts[0, li])
+                f = case.vdi.depth[0, li, :n, 0]
+                b = case.vdi.depth[0, li, :n, 1]
+                q = 4000
+                pts = np.concatenate([f, b, np.float32([-1.0, 1.0])])
+                d0 = np.where(rng.random(q) < 0.3, rng.choice(pts, q), rng.uniform(-1, 1, q)).astype(np.float32)
+                d1 = np.where(rng.random(q) < 0.3, rng.choice(pts, q), rng.uniform(-1, 1, q)).astype(np.float32)
+                inc = (rng.random(q) < 0.5).astype(np.int32)
+                lo, hi = np.minimum(d0, d1), np.maximum(d0, d1)
+                de = np.where(inc == 1, lo, hi).astype(np.float32)
+                dx = np.where(inc == 1, hi, lo).astype(np.float32)
+                seed = rng.integers(-1, ns + 1, q).astype(np.int32)
+                expect = np.array([orc.first_index(f, b, de[i], dx[i], bool(inc[i])) for i in range(q)])
+                for mode in (0, 1, 2):
+                    res = torch.zeros(q, dtype=torch.int32, device="cuda")
+                    t = lambda a: torch.from_numpy(a).cuda()
+                    V.vdi_search_first(vdi, li, mode, t(de), t(dx), t(seed), t(inc), res)
+                    torch.cuda.synchronize()
+                    assert np.array_equal(res.cpu().numpy(), expect), (ns, li, mode)
+        finally:
+            V.vdi_destroy(vdi)
+
+
+@pytest.mark.parametrize("fmt", [0, 1])
+def test_create_download_roundtrip_and_grid(V, ctx, orc, fmt):
+    case = random_case(45, 27, 7, seed=5)  # grid cells: ragged in x and y
+    vdi = V.vdi_create(ctx, case.gpu_desc(V, fmt, T=8, nz=12), case.vdi.rgba, case.vdi.depth, None)
+    try:
+        rgba, depth, counts, grid = V.vdi_download(vdi, 45, 27, 7)
+        assert np.array_equal(counts, case.vdi.counts)
+        valid = np.arange(7)[None, None, :] < case.vdi.counts[:, :, None]
+        assert np.array_equal(depth[valid], case.vdi.depth[valid])
+        assert np.all(np.isinf(depth[~valid]))
+        tol = 2e-6 if fmt == 0 else 2e-3
+        assert np.abs(rgba[valid] - case.vdi.rgba[valid]).max() < tol
+        assert np.all(rgba[~valid] == 0)
+        ref = orc.grid_counts(case.oracle_scene(orc), 8, 12)
+        assert np.array_equal(grid, ref)
+    finally:
+        V.vdi_destroy(vdi)
+
+
+def test_empty_vdi_and_view_that_misses(V, ctx):
+    case = random_case(16, 16, 4, seed=0, fill=0.0)
+    vdi = V.vdi_create(ctx, case.gpu_desc(V, 0), case.vdi.rgba, case.vdi.depth, case.vdi.counts)
+    try:
+        cn = S.orbit_camera(case.bmin, case.bmax, 1.0, az_deg=20)
+        assert np.all(gpu_render(V, vdi, cn, 40, 40) == 0)
+    finally:
+        V.vdi_destroy(vdi)
+    case = random_case(16, 16, 4, seed=1)
+    vdi = V.vdi_create(ctx, case.gpu_desc(V, 0), case.vdi.rgba, case.vdi.depth, case.vdi.counts)
+    try:
+        away = S.Camera(S.look_at(case.cam_o.eye, 2 * case.cam_o.eye - 0.5), case.cam_o.proj, case.cam_o.eye)
+        assert np.all(gpu_render(V, vdi, away, 40, 40) == 0)
+    finally:
+        V.vdi_destroy(vdi)
+
+
+def test_invalid_inputs_are_reported(V, ctx):
+    case = random_case(8, 8, 4, seed=2, fill=1.0)
+    bad = case.vdi.depth.copy()
+    bad[3, 3, 0] = (0.5, 0.1)  # front behind back
+    with pytest.raises(V.VdiError) as e:
+        V.vdi_create(ctx, case.gpu_desc(V, 0), case.vdi.rgba, bad, case.vdi.counts)
+    assert e.value.status == 4
+    badc = case.vdi.rgba.copy()
+    badc[2, 2, 0] = (0.9, 0.1, 0.1, 0.5)  # rgb above alpha: not premultiplied
+    with pytest.raises(V.VdiError) as e:
+        V.vdi_create(ctx, case.gpu_desc(V, 0), badc, case.vdi.depth, case.vdi.counts)
+    assert e.value.status == 1
+    vdi = V.vdi_create(ctx, case.gpu_desc(V, 0), case.vdi.rgba, case.vdi.depth, case.vdi.counts)
+    try:
+        out = torch.zeros((4, 4, 4), device="cuda")
+        cam = S.orbit_camera(case.bmin, case.bmax, 1.0)
+        for args in [(0, 4, 1, 1), (4, 4, 0, 1), (4, 4, 1, 17)]:
+            with pytest.raises(V.VdiError):
+                V.vdi_render(vdi, V.camera(cam.view, cam.proj), args[0], args[1], args[2], args[3], out)
+    finally:
+        V.vdi_destroy(vdi)
