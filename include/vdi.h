@@ -185,6 +185,51 @@ vdi_status vdi_render(vdi_t *vdi, const vdi_camera *view, int W, int H, int d_i,
 vdi_status vdi_render_ex(vdi_t *vdi, const vdi_camera *view, int W, int H, int d_i, int d_r,
                          void *out_rgba, int out_fmt, const vdi_render_opts *opts, void *stream);
 
+/* ---- generation ----------------------------------------------------------
+ * Build a VDI from a scalar volume (Section 3) with the homogeneity
+ * criterion of Eq. 1 at a fixed sensitivity gamma = tau: along each V_O
+ * pixel-centre ray (clipped to V_O's near/far planes and the volume box),
+ * samples at the midpoints of consecutive intervals of world length `step`
+ * are classified by the transfer function, given opacity
+ * a' = 1 - (1 - alpha_tf)^(step / length_unit), and merged into the current
+ * supersegment while tau > || mean premultiplied colour of the supersegment
+ * - premultiplied colour of the sample ||_2; otherwise a new supersegment
+ * starts.  A fully transparent sample closes the current supersegment; the
+ * n_s-th supersegment absorbs everything that follows.  Rays stop once their
+ * opacity reaches 1 - 2^-12.  Each supersegment stores the exact composite of
+ * its samples, so rendering at V_O reproduces the samples' compositing.
+ * FP32 arithmetic is IEEE round-to-nearest without fused operations, in a
+ * fixed order (supersegment counts and depths are reproducible bit for bit).
+ * Also builds the count grid.  Returns after enqueueing on `stream`. */
+enum { VDI_VOL_U8 = 0, VDI_VOL_U16 = 1, VDI_VOL_F32 = 2 };
+
+typedef struct {
+    int nx, ny, nz;      /* voxels; element (i, j, k) at data[(k * ny + j) * nx + i] */
+    int dtype;           /* VDI_VOL_*; u8 / 255, u16 / 65535 and f32 values are the scalar */
+    const void *data;    /* DEVICE pointer, owned by the caller, read until the work completes */
+    double bbox_min[3];  /* world box the volume fills; voxel centres at (index + 1/2) / n of it, */
+    double bbox_max[3];  /* trilinear interpolation with clamp to edge */
+} vdi_volume;
+
+typedef struct {
+    int n_knots;         /* 2..16 */
+    const float *knots;  /* HOST [n_knots][5]: value, r, g, b, alpha (opacity per length_unit);
+                            values strictly increasing; piecewise linear, constant beyond the ends */
+} vdi_tf;
+
+typedef struct {
+    int w, h, n_s;       /* lists and supersegments per list (1..64) */
+    vdi_camera orig;     /* V_O: an OpenGL perspective frustum */
+    float tau;           /* gamma of Eq. 1 (>= 0) */
+    double step;         /* world sampling step (> 0) */
+    double length_unit;  /* world length the stored and transfer-function alphas refer to */
+    int colour_fmt;      /* VDI_F32 or VDI_F16 */
+    int grid_tile, grid_nz; /* count grid (0 -> 8, 20) */
+} vdi_gen_params;
+
+vdi_status vdi_generate(vdi_ctx *ctx, const vdi_volume *vol, const vdi_tf *tf, const vdi_gen_params *params,
+                        void *stream, vdi_t **out);
+
 /* ---- diagnostics --------------------------------------------------------
  * Run the device first-supersegment search on a batch of queries against
  * list `list` of `vdi` (Algorithm 2 and the ablation searches).  Device

@@ -69,11 +69,10 @@ def lib():
         L.orc_upsample.argtypes = [P, C.c_int, C.c_int, P, C.c_int, C.c_int]
         L.orc_first_index.argtypes = [P, P, C.c_int, C.c_float, C.c_float, C.c_int]
         L.orc_first_index.restype = C.c_int
-        if hasattr(L, "orc_generate"):
-            L.orc_generate.argtypes = [P, P, P, P, C.c_int, C.c_int, C.c_int, C.c_double,
-                                       C.c_double, C.c_double, C.c_int, P, P, P, C.c_int]
-            L.orc_dvr.argtypes = [P, P, P, P, C.c_int, C.c_int, C.c_double, C.c_double,
-                                  C.c_int, P, C.c_int]
+        L.orc_generate.argtypes = [P, P, C.c_int, P, P, C.c_int, C.c_int, C.c_int, C.c_double,
+                                   C.c_double, C.c_double, C.c_int, P, P, P, C.c_int]
+        L.orc_dvr.argtypes = [P, P, C.c_int, P, P, C.c_int, C.c_int, C.c_double, C.c_double,
+                              C.c_int, P, P, C.c_int]
         _lib = L
     return _lib
 
@@ -193,3 +192,54 @@ def first_index(f, b, d_entry, d_exit, increasing=True):
     b = np.ascontiguousarray(b, np.float32)
     return lib().orc_first_index(_ptr(f), _ptr(b), len(f), float(d_entry), float(d_exit),
                                  1 if increasing else 0)
+
+
+class Volume:
+    """A scalar volume filling the box [bmin, bmax]; data[z, y, x] of uint8, uint16 or float32."""
+
+    def __init__(self, data, bmin, bmax):
+        self.data = np.ascontiguousarray(data)
+        dt = {np.dtype(np.uint8): 0, np.dtype(np.uint16): 1, np.dtype(np.float32): 2}[self.data.dtype]
+        v = OrcVolume()
+        v.nz, v.ny, v.nx = self.data.shape
+        v.dtype = dt
+        v.data = self.data.ctypes.data_as(C.c_void_p)
+        v.bmin = (C.c_double * 3)(*map(float, bmin))
+        v.bmax = (C.c_double * 3)(*map(float, bmax))
+        self.v = v
+
+
+def generate(volume, knots, view, proj, w, h, ns, tau, step, u, fp32=False, nthreads=None):
+    """VDI generation (Eq. 1, fixed gamma = tau).  Returns VdiArrays-like (rgba, depth, counts)."""
+    nthreads = nthreads or os.cpu_count()
+    knots = np.ascontiguousarray(knots, np.float32)
+    rgba = np.zeros((h, w, ns, 4), np.float32)
+    depth = np.zeros((h, w, ns, 2), np.float32)
+    counts = np.zeros((h, w), np.int32)
+    rc = lib().orc_generate(C.byref(volume.v), _ptr(knots), len(knots), _ptr(_cmarr(view)), _ptr(_cmarr(proj)),
+                            w, h, ns, float(tau), float(step), float(u), 1 if fp32 else 0, _ptr(rgba),
+                            _ptr(depth), _ptr(counts), nthreads)
+    assert rc == 0, "unsupported camera or transfer function"
+    return rgba, depth, counts
+
+
+def dvr(volume, knots, view, proj, w, h, step, u, fp32=False, nthreads=None, with_flags=False):
+    """Emission-absorption DVR through the V_O pixel centres at the generation samples.
+
+    With ``with_flags`` also returns per-ray flags marking rays whose sample
+    count floor(L / step) sits within 1e-4 of a rounding boundary."""
+    nthreads = nthreads or os.cpu_count()
+    knots = np.ascontiguousarray(knots, np.float32)
+    out = np.zeros((h * w, 4), np.float64)
+    fl = np.zeros(h * w, np.uint8)
+    rc = lib().orc_dvr(C.byref(volume.v), _ptr(knots), len(knots), _ptr(_cmarr(view)), _ptr(_cmarr(proj)), w, h,
+                       float(step), float(u), 1 if fp32 else 0, _ptr(out), _ptr(fl), nthreads)
+    assert rc == 0
+    return (out, fl) if with_flags else out
+
+
+def _cmarr(m):
+    m = np.asarray(m, np.float64)
+    if m.shape == (4, 4):
+        m = m.T
+    return np.ascontiguousarray(m).reshape(16)

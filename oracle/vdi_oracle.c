@@ -95,7 +95,9 @@ static void mat_vec(const double *A, const double v[4], double out[4]) {
 }
 
 /* Gauss-Jordan elimination with partial pivoting; returns 0 if singular. */
-static int mat_inv(const double *A, double *out) {
+int orc__mat_inv(const double *A, double *out);
+static int mat_inv(const double *A, double *out) { return orc__mat_inv(A, out); }
+int orc__mat_inv(const double *A, double *out) {
     double a[4][8];
     for (int r = 0; r < 4; r++)
         for (int c = 0; c < 4; c++) {

@@ -21,7 +21,7 @@ __all__ = [
     "VDI_F32", "VDI_F16", "VDI_MEM_HOST", "VDI_MEM_DEVICE", "VDI_SEARCH_ALG2", "VDI_SEARCH_BINARY",
     "VDI_SEARCH_LINEAR", "VdiError", "VdiCamera", "VdiDesc", "VdiLayout", "VdiRenderOpts", "load",
     "vdi_ctx_create", "vdi_ctx_destroy", "vdi_layout_bytes", "vdi_create", "vdi_download", "vdi_get_layout",
-    "vdi_destroy", "vdi_render", "vdi_render_ex", "vdi_search_first", "camera", "desc",
+    "vdi_destroy", "vdi_render", "vdi_render_ex", "vdi_search_first", "vdi_generate", "camera", "desc",
 ]
 
 VDI_F32, VDI_F16 = 0, 1
@@ -52,6 +52,21 @@ class VdiLayout(C.Structure):
     _fields_ = [("depth_bytes", C.c_size_t), ("colour_bytes", C.c_size_t), ("grid_bytes", C.c_size_t),
                 ("total_bytes", C.c_size_t), ("paper_bytes", C.c_size_t), ("grid_w", C.c_int),
                 ("grid_h", C.c_int), ("grid_nz", C.c_int), ("n_s_stored", C.c_int)]
+
+
+class VdiVolume(C.Structure):
+    _fields_ = [("nx", C.c_int), ("ny", C.c_int), ("nz", C.c_int), ("dtype", C.c_int), ("data", C.c_void_p),
+                ("bbox_min", C.c_double * 3), ("bbox_max", C.c_double * 3)]
+
+
+class VdiTf(C.Structure):
+    _fields_ = [("n_knots", C.c_int), ("knots", C.c_void_p)]
+
+
+class VdiGenParams(C.Structure):
+    _fields_ = [("w", C.c_int), ("h", C.c_int), ("n_s", C.c_int), ("orig", VdiCamera), ("tau", C.c_float),
+                ("step", C.c_double), ("length_unit", C.c_double), ("colour_fmt", C.c_int),
+                ("grid_tile", C.c_int), ("grid_nz", C.c_int)]
 
 
 class VdiRenderOpts(C.Structure):
@@ -93,6 +108,7 @@ def load(build_if_needed: bool = True):
     _sig(L, "vdi_render", [P, P, C.c_int, C.c_int, C.c_int, C.c_int, P, C.c_int, P])
     _sig(L, "vdi_render_ex", [P, P, C.c_int, C.c_int, C.c_int, C.c_int, P, C.c_int, P, P])
     _sig(L, "vdi_search_first", [P, C.c_int, C.c_int, P, P, P, P, P, C.c_int, P])
+    _sig(L, "vdi_generate", [P, P, P, P, P, C.POINTER(P)])
     _lib = L
     return L
 
@@ -226,3 +242,27 @@ def vdi_search_first(vdi, list_index, search, d_entry, d_exit, seed, increasing,
     n = int(d_entry.numel())
     _check(load().vdi_search_first(vdi, int(list_index), int(search), _dptr(d_entry), _dptr(d_exit), _dptr(seed),
                                    _dptr(increasing), _dptr(result), n, _stream(stream)))
+
+
+_VOL_DTYPE = {"uint8": 0, "uint16": 1, "float32": 2}
+
+
+def vdi_generate(ctx, volume, bbox_min, bbox_max, knots, cam_o: VdiCamera, w, h, n_s, tau, step, length_unit,
+                 colour_fmt=VDI_F32, grid_tile=0, grid_nz=0, stream=None):
+    """volume: torch CUDA tensor [nz, ny, nx] of uint8/uint16/float32; knots: (n, 5) array."""
+    vol = VdiVolume()
+    vol.nz, vol.ny, vol.nx = (int(x) for x in volume.shape)
+    vol.dtype = _VOL_DTYPE[str(volume.dtype).replace("torch.", "")]
+    vol.data = _dptr(volume)
+    vol.bbox_min = (C.c_double * 3)(*map(float, bbox_min))
+    vol.bbox_max = (C.c_double * 3)(*map(float, bbox_max))
+    kn = np.ascontiguousarray(knots, np.float32)
+    tf = VdiTf()
+    tf.n_knots, tf.knots = len(kn), kn.ctypes.data
+    p = VdiGenParams()
+    p.w, p.h, p.n_s, p.orig = int(w), int(h), int(n_s), cam_o
+    p.tau, p.step, p.length_unit = float(tau), float(step), float(length_unit)
+    p.colour_fmt, p.grid_tile, p.grid_nz = int(colour_fmt), int(grid_tile), int(grid_nz)
+    out = P()
+    _check(load().vdi_generate(ctx, C.byref(vol), C.byref(tf), C.byref(p), _stream(stream), C.byref(out)))
+    return out

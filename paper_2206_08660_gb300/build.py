@@ -20,7 +20,7 @@ OUT = os.path.join(HERE, "_build")
 LIB = os.path.join(OUT, "libvdi.so")
 
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
-NVFLAGS = ARCH + ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC,-fvisibility=hidden,-O2",
+NVFLAGS = ARCH + ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC,-fvisibility=hidden,-O2,-ffp-contract=off",
                   "--expt-relaxed-constexpr", "-I" + INCLUDE]
 
 

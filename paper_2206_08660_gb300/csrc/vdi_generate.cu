@@ -1,0 +1,348 @@
+// vdi_generate.cu -- VDI generation from a scalar volume (Section 3, Eq. 1
+// with a fixed sensitivity gamma = tau), one thread per V_O pixel ray.
+//
+// Arithmetic uses explicit round-to-nearest FP32 intrinsics with no fused
+// multiply-add, in a fixed order, so the integer outcome of generation (how
+// many supersegments each list gets and where they start and end) is the
+// reproducible result of IEEE FP32 operations.  The supersegment depths are
+// written straight into the structure-of-arrays device layout; the colour is
+// stored as (rgb / alpha, kappa) where kappa = -log2(segment transmittance)
+// per length unit (the composite over the segment, Section 2.3).
+#include <cuda_fp16.h>
+#include <cuda_runtime.h>
+#include <math.h>
+#include <stdint.h>
+
+#include "../../include/vdi.h"
+#include "vdi_api_internal.h"
+#include "vdi_internal.cuh"
+
+namespace vdi {
+
+struct GenConsts {
+    float E[3], D0[3], Dx[3], Dy[3];  // ray p(t) = E + t (D0 + x Dx + y Dy), t = V_O view depth
+    float t_near, t_far, P22, P23;    // NDC z = P23 / t - P22
+    float bmin[3], bmax[3], ext[3];
+    float step, u, tau, adj_exp;
+    int step_is_u;
+    float kv[16], kc[16][4];
+    int nk;
+    int w, h, ns, nsp;
+    long long nl;
+    int nx, ny, nz, dtype;
+    const void *data;
+    int fmt;
+};
+
+#define ADD __fadd_rn
+#define SUB __fsub_rn
+#define MUL __fmul_rn
+#define DIV __fdiv_rn
+
+__device__ __forceinline__ float lerp_rn(float a, float b, float t) { return ADD(a, MUL(t, SUB(b, a))); }
+
+__device__ __forceinline__ float voxel(const GenConsts &g, int i, int j, int k) {
+    const size_t o = ((size_t)k * g.ny + j) * g.nx + i;
+    if (g.dtype == 0) return DIV((float)__ldg(reinterpret_cast<const uint8_t *>(g.data) + o), 255.f);
+    if (g.dtype == 1) return DIV((float)__ldg(reinterpret_cast<const uint16_t *>(g.data) + o), 65535.f);
+    return __ldg(reinterpret_cast<const float *>(g.data) + o);
+}
+
+__device__ __forceinline__ float trilinear(const GenConsts &g, const float p[3]) {
+    const int n[3] = {g.nx, g.ny, g.nz};
+    int i0[3], i1[3];
+    float fr[3];
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+        const float q = SUB(MUL(DIV(SUB(p[c], g.bmin[c]), g.ext[c]), (float)n[c]), 0.5f);
+        const float fl = floorf(q);
+        fr[c] = SUB(q, fl);
+        const int i = (int)fl;
+        i0[c] = min(max(i, 0), n[c] - 1);
+        i1[c] = min(max(i + 1, 0), n[c] - 1);
+    }
+    const float c00 = lerp_rn(voxel(g, i0[0], i0[1], i0[2]), voxel(g, i1[0], i0[1], i0[2]), fr[0]);
+    const float c10 = lerp_rn(voxel(g, i0[0], i1[1], i0[2]), voxel(g, i1[0], i1[1], i0[2]), fr[0]);
+    const float c01 = lerp_rn(voxel(g, i0[0], i0[1], i1[2]), voxel(g, i1[0], i0[1], i1[2]), fr[0]);
+    const float c11 = lerp_rn(voxel(g, i0[0], i1[1], i1[2]), voxel(g, i1[0], i1[1], i1[2]), fr[0]);
+    return lerp_rn(lerp_rn(c00, c10, fr[1]), lerp_rn(c01, c11, fr[1]), fr[2]);
+}
+
+__device__ __forceinline__ void classify(const GenConsts &g, float v, float out[4]) {
+    const int last = g.nk - 1;
+    if (v <= g.kv[0]) {
+#pragma unroll
+        for (int c = 0; c < 4; ++c) out[c] = g.kc[0][c];
+        return;
+    }
+    if (v >= g.kv[last]) {
+#pragma unroll
+        for (int c = 0; c < 4; ++c) out[c] = g.kc[last][c];
+        return;
+    }
+    int i = 0;
+    while (!(v < g.kv[i + 1])) ++i;
+    const float s = DIV(SUB(v, g.kv[i]), SUB(g.kv[i + 1], g.kv[i]));
+#pragma unroll
+    for (int c = 0; c < 4; ++c) out[c] = lerp_rn(g.kc[i][c], g.kc[i + 1][c], s);
+}
+
+struct SegWriter {
+    int nseg;
+    float pf, pb;      // pending even slot (depth)
+    float4 pc;         // pending even slot (colour)
+};
+
+__device__ __forceinline__ unsigned h2bits(float a, float b) {
+    __half2 h = __floats2half2_rn(a, b);
+    return *reinterpret_cast<unsigned *>(&h);
+}
+
+__device__ __forceinline__ void write_pair(const GenConsts &g, float4 *depth, void *colour, long long li, int k,
+                                           float f0, float b0, float4 c0, float f1, float b1, float4 c1) {
+    depth[(size_t)k * g.nl + li] = make_float4(f0, b0, f1, b1);
+    if (g.fmt == 0) {
+        float4 *cp = reinterpret_cast<float4 *>(colour);
+        cp[(size_t)(2 * k) * g.nl + li] = c0;
+        cp[(size_t)(2 * k + 1) * g.nl + li] = c1;
+    } else {
+        uint4 q;
+        q.x = h2bits(c0.x, c0.y);
+        q.y = h2bits(c0.z, c0.w);
+        q.z = h2bits(c1.x, c1.y);
+        q.w = h2bits(c1.z, c1.w);
+        reinterpret_cast<uint4 *>(colour)[(size_t)k * g.nl + li] = q;
+    }
+}
+
+__global__ void __launch_bounds__(256) generate_kernel(const GenConsts g, float4 *__restrict__ depth,
+                                                       void *__restrict__ colour) {
+    const int px = blockIdx.x * 32 + (threadIdx.x & 31);
+    const int py = blockIdx.y * 8 + (threadIdx.x >> 5);
+    if (px >= g.w || py >= g.h) return;
+    const long long li = (long long)py * g.w + px;
+    SegWriter sw;
+    sw.nseg = 0;
+    sw.pf = sw.pb = INFINITY;
+    sw.pc = make_float4(0.f, 0.f, 0.f, 0.f);
+
+    auto emit = [&](float f, float b, float4 col) {
+        const int j = sw.nseg++;
+        if ((j & 1) == 0) {
+            sw.pf = f;
+            sw.pb = b;
+            sw.pc = col;
+        } else {
+            write_pair(g, depth, colour, li, j >> 1, sw.pf, sw.pb, sw.pc, f, b, col);
+        }
+    };
+
+    // ---- ray through the pixel centre, clipped to V_O near/far and the box
+    const float x = SUB(DIV(MUL(2.f, ADD((float)px, 0.5f)), (float)g.w), 1.f);
+    const float y = SUB(1.f, DIV(MUL(2.f, ADD((float)py, 0.5f)), (float)g.h));
+    float dir[3];
+#pragma unroll
+    for (int c = 0; c < 3; ++c) dir[c] = ADD(ADD(g.D0[c], MUL(x, g.Dx[c])), MUL(y, g.Dy[c]));
+    const float len = __fsqrt_rn(ADD(ADD(MUL(dir[0], dir[0]), MUL(dir[1], dir[1])), MUL(dir[2], dir[2])));
+    float t0 = g.t_near, t1 = g.t_far;
+    bool hit = true;
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+        if (dir[c] != 0.f) {
+            float ta = DIV(SUB(g.bmin[c], g.E[c]), dir[c]), tb = DIV(SUB(g.bmax[c], g.E[c]), dir[c]);
+            if (ta > tb) {
+                const float s = ta;
+                ta = tb;
+                tb = s;
+            }
+            if (ta > t0) t0 = ta;
+            if (tb < t1) t1 = tb;
+        } else if (g.E[c] < g.bmin[c] || g.E[c] > g.bmax[c]) {
+            hit = false;
+        }
+    }
+    long long K = 0;
+    float dt = 0.f;
+    if (hit && t0 < t1) {
+        const float L = MUL(SUB(t1, t0), len);
+        K = (long long)floorf(DIV(L, g.step));
+        dt = DIV(g.step, len);
+    }
+
+    // ---- march, segment (Eq. 1), composite
+    bool open = false;
+    float t_start = 0.f, t_end = 0.f, Tseg = 1.f, Tray = 1.f;
+    float mean[3] = {0.f, 0.f, 0.f}, Cacc[3] = {0.f, 0.f, 0.f};
+    int cnt = 0;
+    const float tau2 = MUL(g.tau, g.tau);
+    auto close = [&]() {
+        const float f = SUB(DIV(g.P23, t_start), g.P22);
+        const float b = SUB(DIV(g.P23, t_end), g.P22);
+        const float aacc = 1.f - Tseg;
+        const float Lu = (t_end - t_start) * len / g.u;  // world length in length units
+        const float ia = aacc > 0.f ? 1.f / aacc : 0.f;
+        float kappa = (Lu > 0.f) ? -log2f(Tseg) / Lu : 0.f;
+        emit(f, b, make_float4(fminf(Cacc[0] * ia, 1.f), fminf(Cacc[1] * ia, 1.f), fminf(Cacc[2] * ia, 1.f), kappa));
+        open = false;
+    };
+    for (long long k = 0; k < K; ++k) {
+        const float fk = (float)k;
+        const float ta = ADD(t0, MUL(fk, dt));
+        const float tm = ADD(t0, MUL(ADD(fk, 0.5f), dt));
+        const float tb = ADD(t0, MUL((float)(k + 1), dt));
+        float p[3];
+#pragma unroll
+        for (int c = 0; c < 3; ++c) p[c] = ADD(g.E[c], MUL(tm, dir[c]));
+        float tf[4];
+        classify(g, trilinear(g, p), tf);
+        const float a = g.step_is_u ? tf[3] : 1.f - powf(1.f - tf[3], g.adj_exp);
+        if (!(a > 0.f)) {
+            if (open && sw.nseg < g.ns - 1) close();
+            continue;
+        }
+        const float xc[3] = {MUL(tf[0], a), MUL(tf[1], a), MUL(tf[2], a)};
+        if (open && sw.nseg < g.ns - 1) {
+            const float d0 = SUB(mean[0], xc[0]), d1 = SUB(mean[1], xc[1]), d2 = SUB(mean[2], xc[2]);
+            const float dist2 = ADD(ADD(MUL(d0, d0), MUL(d1, d1)), MUL(d2, d2));
+            if (!(tau2 > dist2)) close();
+        }
+        if (!open) {
+            open = true;
+            t_start = ta;
+            cnt = 0;
+            Tseg = 1.f;
+#pragma unroll
+            for (int c = 0; c < 3; ++c) mean[c] = Cacc[c] = 0.f;
+        }
+        ++cnt;
+#pragma unroll
+        for (int c = 0; c < 3; ++c) {
+            mean[c] = ADD(mean[c], DIV(SUB(xc[c], mean[c]), (float)cnt));
+            Cacc[c] = ADD(Cacc[c], MUL(Tseg, xc[c]));
+        }
+        Tseg = MUL(Tseg, SUB(1.f, a));
+        t_end = tb;
+        Tray = MUL(Tray, SUB(1.f, a));
+        if (Tray <= kErtT) break;
+    }
+    if (open) close();
+
+    // ---- pad the remaining slots
+    const float4 zero = make_float4(0.f, 0.f, 0.f, 0.f);
+    int j = sw.nseg;
+    if (j & 1) {
+        write_pair(g, depth, colour, li, j >> 1, sw.pf, sw.pb, sw.pc, INFINITY, INFINITY, zero);
+        ++j;
+    }
+    for (; j < g.nsp; j += 2)
+        write_pair(g, depth, colour, li, j >> 1, INFINITY, INFINITY, zero, INFINITY, INFINITY, zero);
+}
+
+#undef ADD
+#undef SUB
+#undef MUL
+#undef DIV
+
+cudaError_t launch_grid(const DevVdi &v, uint32_t *grid, cudaStream_t st);
+
+}  // namespace vdi
+
+using namespace vdi;
+
+#define VDI_API extern "C" __attribute__((visibility("default")))
+
+static double pe(const double *m, int r, int c) { return m[c * 4 + r]; }
+
+VDI_API vdi_status vdi_generate(vdi_ctx *ctx, const vdi_volume *vol, const vdi_tf *tf, const vdi_gen_params *prm,
+                                void *stream, vdi_t **out) {
+    if (!ctx || !vol || !tf || !prm || !out) return fail(VDI_ERR_INVALID_ARG, "NULL argument");
+    *out = nullptr;
+    if (!vol->data || vol->nx < 1 || vol->ny < 1 || vol->nz < 1 || vol->dtype < 0 || vol->dtype > 2)
+        return fail(VDI_ERR_INVALID_ARG, "bad volume");
+    if (tf->n_knots < 2 || tf->n_knots > 16 || !tf->knots) return fail(VDI_ERR_INVALID_ARG, "n_knots in 2..16");
+    for (int k = 0; k < tf->n_knots; ++k) {
+        const float *kn = tf->knots + 5 * k;
+        for (int c = 0; c < 5; ++c)
+            if (!isfinite(kn[c])) return fail(VDI_ERR_INVALID_ARG, "non-finite knot");
+        if (k > 0 && !(kn[0] > tf->knots[5 * (k - 1)])) return fail(VDI_ERR_INVALID_ARG, "knot values must increase");
+        if (kn[4] < 0.f || kn[4] > 1.f) return fail(VDI_ERR_INVALID_ARG, "knot alpha outside [0,1]");
+        for (int c = 1; c < 4; ++c)
+            if (kn[c] < 0.f || kn[c] > 1.f) return fail(VDI_ERR_INVALID_ARG, "knot colour outside [0,1]");
+    }
+    if (!(prm->step > 0.0) || !(prm->tau >= 0.f) || !isfinite(prm->tau))
+        return fail(VDI_ERR_INVALID_ARG, "step must be > 0 and tau >= 0");
+    const double *P = prm->orig.proj;
+    if (!(pe(P, 3, 0) == 0 && pe(P, 3, 1) == 0 && pe(P, 3, 2) == -1 && pe(P, 3, 3) == 0 && pe(P, 2, 0) == 0 &&
+          pe(P, 2, 1) == 0 && pe(P, 0, 1) == 0 && pe(P, 1, 0) == 0 && pe(P, 0, 3) == 0 && pe(P, 1, 3) == 0))
+        return fail(VDI_ERR_UNSUPPORTED, "generation needs an OpenGL perspective frustum for V_O");
+    vdi_desc d{};
+    d.w = prm->w;
+    d.h = prm->h;
+    d.n_s = prm->n_s;
+    d.orig = prm->orig;
+    for (int k = 0; k < 3; ++k) {
+        d.bbox_min[k] = vol->bbox_min[k];
+        d.bbox_max[k] = vol->bbox_max[k];
+    }
+    d.length_unit = prm->length_unit;
+    d.colour_fmt = prm->colour_fmt;
+    d.grid_tile = prm->grid_tile;
+    d.grid_nz = prm->grid_nz;
+    double Vi[16];
+    if (!mat4_inv(prm->orig.view, Vi)) return fail(VDI_ERR_INVALID_ARG, "V_O view is singular");
+    cudaSetDevice(ctx->device);
+    vdi_t *v = nullptr;
+    vdi_status st_ = alloc_vdi(ctx, &d, &v);
+    if (st_ != VDI_OK) return st_;
+
+    GenConsts g{};
+    const double dv0[3] = {pe(P, 0, 2) / pe(P, 0, 0), pe(P, 1, 2) / pe(P, 1, 1), -1.0};
+    for (int r = 0; r < 3; ++r) {
+        g.E[r] = (float)(pe(Vi, r, 3) / pe(Vi, 3, 3));
+        double s0 = 0.0;
+        for (int c = 0; c < 3; ++c) s0 += pe(Vi, r, c) * dv0[c];
+        g.D0[r] = (float)s0;
+        g.Dx[r] = (float)(pe(Vi, r, 0) * (1.0 / pe(P, 0, 0)));
+        g.Dy[r] = (float)(pe(Vi, r, 1) * (1.0 / pe(P, 1, 1)));
+        g.bmin[r] = (float)vol->bbox_min[r];
+        g.bmax[r] = (float)vol->bbox_max[r];
+        g.ext[r] = g.bmax[r] - g.bmin[r];  // one IEEE float subtraction (host code is built without contraction)
+    }
+    g.P22 = (float)pe(P, 2, 2);
+    g.P23 = (float)pe(P, 2, 3);
+    g.t_near = (float)(pe(P, 2, 3) / (pe(P, 2, 2) - 1.0));
+    g.t_far = (float)(pe(P, 2, 3) / (pe(P, 2, 2) + 1.0));
+    g.step = (float)prm->step;
+    g.u = (float)prm->length_unit;
+    g.tau = prm->tau;
+    g.step_is_u = g.step == g.u;
+    g.adj_exp = g.step / g.u;
+    g.nk = tf->n_knots;
+    for (int k = 0; k < g.nk; ++k) {
+        g.kv[k] = tf->knots[5 * k];
+        for (int c = 0; c < 4; ++c) g.kc[k][c] = tf->knots[5 * k + 1 + c];
+    }
+    g.w = d.w;
+    g.h = d.h;
+    g.ns = d.n_s;
+    g.nsp = v->dv.nsp;
+    g.nl = v->dv.nl;
+    g.nx = vol->nx;
+    g.ny = vol->ny;
+    g.nz = vol->nz;
+    g.dtype = vol->dtype;
+    g.data = vol->data;
+    g.fmt = d.colour_fmt;
+    cudaStream_t st = (cudaStream_t)stream;
+    dim3 grid(div_up(d.w, 32), div_up(d.h, 8));
+    generate_kernel<<<grid, 256, 0, st>>>(g, reinterpret_cast<float4 *>(v->depth_mem), v->colour_mem);
+    cudaError_t e = cudaGetLastError();
+    if (e == cudaSuccess) e = launch_grid(v->dv, v->grid_mem, st);
+    if (e != cudaSuccess) {
+        cudaStreamSynchronize(st);
+        free_vdi(v);
+        return cuda_fail(e, "generate");
+    }
+    *out = v;
+    return VDI_OK;
+}
