@@ -19,6 +19,8 @@
 
 namespace vdi {
 
+constexpr long long kMaxSamples = 1 << 22;  // per ray; the host rejects steps that would need more
+
 struct GenConsts {
     float E[3], D0[3], Dx[3], Dy[3];  // ray p(t) = E + t (D0 + x Dx + y Dy), t = V_O view depth
     float t_near, t_far, P22, P23;    // NDC z = P23 / t - P22
@@ -81,7 +83,7 @@ __device__ __forceinline__ void classify(const GenConsts &g, float v, float out[
         return;
     }
     int i = 0;
-    while (!(v < g.kv[i + 1])) ++i;
+    while (i < last - 1 && !(v < g.kv[i + 1])) ++i;
     const float s = DIV(SUB(v, g.kv[i]), SUB(g.kv[i + 1], g.kv[i]));
 #pragma unroll
     for (int c = 0; c < 4; ++c) out[c] = lerp_rn(g.kc[i][c], g.kc[i + 1][c], s);
@@ -165,7 +167,8 @@ __global__ void __launch_bounds__(256) generate_kernel(const GenConsts g, float4
     float dt = 0.f;
     if (hit && t0 < t1) {
         const float L = MUL(SUB(t1, t0), len);
-        K = (long long)floorf(DIV(L, g.step));
+        const float kq = floorf(DIV(L, g.step));
+        K = kq < (float)kMaxSamples ? (long long)kq : kMaxSamples;
         dt = DIV(g.step, len);
     }
 
@@ -271,6 +274,12 @@ VDI_API vdi_status vdi_generate(vdi_ctx *ctx, const vdi_volume *vol, const vdi_t
     }
     if (!(prm->step > 0.0) || !(prm->tau >= 0.f) || !isfinite(prm->tau))
         return fail(VDI_ERR_INVALID_ARG, "step must be > 0 and tau >= 0");
+    {
+        double diag = 0.0;
+        for (int k = 0; k < 3; ++k) diag += (vol->bbox_max[k] - vol->bbox_min[k]) * (vol->bbox_max[k] - vol->bbox_min[k]);
+        if (!(sqrt(diag) / prm->step < (double)kMaxSamples))
+            return fail(VDI_ERR_INVALID_ARG, "step too small: more than %lld samples per ray", kMaxSamples);
+    }
     const double *P = prm->orig.proj;
     if (!(pe(P, 3, 0) == 0 && pe(P, 3, 1) == 0 && pe(P, 3, 2) == -1 && pe(P, 3, 3) == 0 && pe(P, 2, 0) == 0 &&
           pe(P, 2, 1) == 0 && pe(P, 0, 1) == 0 && pe(P, 1, 0) == 0 && pe(P, 0, 3) == 0 && pe(P, 1, 3) == 0))
