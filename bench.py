@@ -1,0 +1,372 @@
+#!/usr/bin/env python
+"""Benchmark: VDI raycasting frames/s at 1920x1080 on the large mixing-layer workload.
+
+Workload ("large"): a 1024^3 uint8 mixing-layer volume (tanh interface at mid
+height perturbed by 64 Fourier modes) -> GPU vdi_generate at 1920x1080,
+N_S = 20, FP16 colour / FP32 depth.  One step renders the resident VDI at
+1920x1080 from new views rotated 10, 20 and 30 degrees about the volume's
+vertical axis, plus the previews (D_I, D_R) = (2, 2) and (4, 4) at 30 degrees:
+5 frames.  L2 is flushed (256 MiB write) between steps; each step's kernels
+are timed with CUDA events on the launching stream.
+
+Also reported: the HBM roofline of the exact-render kernel (unique VDI bytes
+one frame needs, from the instrumented touch bitmap, divided by the kernel's
+event-timed duration), nvidia-smi clocks during the timed region, an
+end-to-end number through the public API with images read back to pinned host
+memory, and the FP64 CPU oracle timed on a bounded sample of the same frames.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+import vdi_synth as S  # noqa: E402
+
+METRIC = "VDI raycast frames/s & Grays/s at 1920x1080 (HBM roofline %); serving p50/p99 ms"
+
+WORKLOADS = {
+    "large": dict(name="mixing-layer 1024^3 u8 -> VDI 1920x1080 N_S=20 FP16 colour; renders 1920x1080 at "
+                       "10/20/30 deg + previews (D_I,D_R)=(2,2),(4,4) at 30 deg",
+                  n=1024, vol="mixing", dtype=np.uint8, tf="interface", w=1920, h=1080, ns=20, tau=0.01, fmt=1,
+                  W=1920, H=1080, el=25.0, zoom=1.0,
+                  frames=[(10.0, 1, 1), (20.0, 1, 1), (30.0, 1, 1), (30.0, 2, 2), (30.0, 4, 4)]),
+    "plain": dict(name="value-noise 256^3 u16 -> VDI 1280x720 N_S=20 FP32; renders 1280x720 at 0/5/15/30 deg, zoom 1.2",
+                  n=256, vol="noise", dtype=np.uint16, tf="sparse", w=1280, h=720, ns=20, tau=0.01, fmt=0,
+                  W=1280, H=720, el=20.0, zoom=1.2,
+                  frames=[(0.0, 1, 1), (5.0, 1, 1), (15.0, 1, 1), (30.0, 1, 1)]),
+    "tiny": dict(name="blobs 64^3 f32 -> VDI 128x128 N_S=8 FP32; render 128x128 at 10 deg",
+                 n=64, vol="blobs", dtype=np.float32, tf="dense", w=128, h=128, ns=8, tau=0.02, fmt=0,
+                 W=128, H=128, el=15.0, zoom=1.0, frames=[(10.0, 1, 1)]),
+}
+
+
+def make_volume(wl, seed=0):
+    if wl["vol"] == "mixing":
+        return S.mixing_layer_volume(wl["n"], seed=seed, dtype=wl["dtype"])
+    if wl["vol"] == "noise":
+        return S.value_noise_volume(wl["n"], seed=seed, dtype=wl["dtype"])
+    return S.blobs_volume(wl["n"], seed=seed)
+
+
+def cameras(wl, bmin, bmax):
+    cam_o = S.orbit_camera(bmin, bmax, wl["w"] / wl["h"], az_deg=0.0, el_deg=wl["el"])
+    views = [S.orbit_camera(bmin, bmax, wl["W"] / wl["H"], az_deg=az, el_deg=wl["el"], zoom=wl["zoom"])
+             for (az, _, _) in wl["frames"]]
+    return cam_o, views
+
+
+def peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(p) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+def render_kernel_hash() -> str:
+    h = hashlib.sha1()
+    for fn in ("vdi_render.cu", "vdi_internal.cuh"):
+        with open(os.path.join(ROOT, "paper_2206_08660_gb300", "csrc", fn), "rb") as f:
+            h.update(f.read())
+    return h.hexdigest()[:12]
+
+
+def recorded_traffic(workload: str):
+    """DRAM bytes per exact-render launch from the committed ncu summary, if it
+    was taken on the current kernel source; else None."""
+    p = os.path.join(ROOT, "profiles", f"render_exact_{workload}.md")
+    if not os.path.exists(p):
+        return None
+    want = render_kernel_hash()
+    for line in open(p):
+        if line.startswith("traffic_bytes_per_launch:"):
+            parts = line.split()
+            if len(parts) >= 4 and parts[2] == "kernel_hash" and parts[3] == want:
+                return int(parts[1])
+    return None
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled every 200 ms."""
+
+    Q = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.hw_slowdown,"
+         "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+         "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.proc = None
+        self.lines = []
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(gpu_index), f"--query-gpu={self.Q}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except Exception:
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        sm, smax, reasons = [], 0.0, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            f = [x.strip() for x in ln.split(",")]
+            if len(f) < 7:
+                continue
+            try:
+                sm.append(float(f[0]))
+                smax = max(smax, float(f[1]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, f[3:7]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        if not sm:
+            return None
+        return {"sm_mhz": float(np.median(sm)), "sm_max_mhz": smax, "reasons": sorted(reasons), "samples": len(sm)}
+
+
+class OracleLeg:
+    """The FP64 CPU oracle on the same workload, for the CPU baseline and the
+    reference arm.  The oracle renders its own VDI, made by the oracle's FP32
+    generation (which matches the GPU's supersegments bit for bit)."""
+
+    def __init__(self, wl, vol, bmin, bmax, u, cam_o, views):
+        import oracle
+
+        self.o = oracle
+        kn = S.tf_knots(wl["tf"])
+        rgba, depth, counts = oracle.generate(oracle.Volume(vol, bmin, bmax), kn, cam_o.view, cam_o.proj, wl["w"],
+                                              wl["h"], wl["ns"], wl["tau"], u, u, fp32=True)
+        self.sc = oracle.Scene(S.VdiArrays(wl["w"], wl["h"], wl["ns"], rgba, depth, counts), cam_o.view, cam_o.proj,
+                               bmin, bmax, u)
+        self.wl, self.views = wl, views
+        self.threads = os.cpu_count() or 1
+
+    def run(self, R, rng):
+        """R random rays of every frame; returns (seconds measured, seconds extrapolated to full frames)."""
+        measured = full = 0.0
+        for (az, d_i, d_r), cn in zip(self.wl["frames"], self.views):
+            Wr, Hr = -(-self.wl["W"] // d_i), -(-self.wl["H"] // d_i)
+            pix = rng.integers(0, Wr * Hr, size=min(R, Wr * Hr)).astype(np.int32)
+            t = time.perf_counter()
+            if d_r == 1:
+                self.o.render_exact(self.sc, cn.view, cn.proj, Wr, Hr, pix=pix, nthreads=self.threads)
+            else:
+                self.o.render_preview(self.sc, cn.view, cn.proj, Wr, Hr, d_r, pix=pix, nthreads=self.threads)
+            dt = time.perf_counter() - t
+            measured += dt
+            full += dt / len(pix) * (Wr * Hr)
+        return measured, full
+
+    def rays_for_budget(self, budget_s, rng, probe=512):
+        m, _ = self.run(probe, rng)
+        return int(min(200000, max(probe, probe * budget_s / max(m, 1e-6))))
+
+    def sample_text(self, R):
+        return (f"{R} random rays from each of the {len(self.wl['frames'])} frames per step, timed and extrapolated "
+                f"to full frames; oracle VDI from the oracle's own FP32 generation")
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default="large", choices=list(WORKLOADS))
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--cpu-budget", type=float, default=15.0, help="seconds of oracle work for cpu_baseline")
+    args = ap.parse_args()
+    wl = WORKLOADS[args.workload]
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local_rank = int(os.environ.get("LOCAL_RANK", "0"))
+
+    vol = make_volume(wl)
+    bmin, bmax = S.bbox_for_dims(vol.shape)
+    u = 1.0 / max(vol.shape)
+    cam_o, views = cameras(wl, bmin, bmax)
+    frames_per_step = len(wl["frames"])
+    config = {"workload": wl["name"], "vdi": f"{wl['w']}x{wl['h']} N_S={wl['ns']} "
+                                             f"{'FP16' if wl['fmt'] else 'FP32'} colour, FP32 depth",
+              "frames_per_step": frames_per_step, "image": f"{wl['W']}x{wl['H']}",
+              "l2": "flushed between steps (256 MiB write)", "out_fmt": "f16", "search": "Algorithm 2"}
+
+    if args.impl == "reference":
+        if rank != 0:
+            return
+        leg = OracleLeg(wl, vol, bmin, bmax, u, cam_o, views)
+        rng = np.random.default_rng(0)
+        R = leg.rays_for_budget(2.0, rng)
+        t_all = []
+        for i in range(args.warmup + args.steps):
+            _, full = leg.run(R, rng)
+            if i >= args.warmup:
+                t_all.append(full)
+        ms = 1e3 * float(np.mean(t_all))
+        val = frames_per_step / (ms / 1e3)
+        cores, sample = leg.threads, leg.sample_text(R)
+        print(json.dumps({"impl": "reference", "metric": METRIC, "value": val, "unit": "frames/s", "n_gpus": 1,
+                          "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
+                          "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+                          "config": config,
+                          "cpu_baseline": {"value": val, "unit": "frames/s", "cores": cores, "kind": "oracle",
+                                           "sample": sample},
+                          "e2e": {"value": val, "unit": "frames/s", "h2d_bytes_per_step": 0,
+                                  "d2h_bytes_per_step": 0}}))
+        return
+
+    import torch
+
+    import paper_2206_08660_gb300 as V
+
+    torch.cuda.set_device(local_rank)
+    if world > 1:
+        import torch.distributed as dist
+
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local_rank))
+    dev = torch.device("cuda", local_rank)
+    V.load()
+    ctx = V.vdi_ctx_create(local_rank)
+    stream = torch.cuda.current_stream()
+    kn = S.tf_knots(wl["tf"])
+    vol_d = torch.from_numpy(vol).to(dev)
+    t = time.perf_counter()
+    vdi = V.vdi_generate(ctx, vol_d, bmin, bmax, kn, V.camera(cam_o.view, cam_o.proj), wl["w"], wl["h"], wl["ns"],
+                         wl["tau"], u, u, wl["fmt"])
+    torch.cuda.synchronize()
+    gen_s = time.perf_counter() - t
+    del vol_d
+    torch.cuda.empty_cache()
+    layout = V.vdi_get_layout(vdi)
+    cams = [V.camera(c.view, c.proj) for c in views]
+    W, H = wl["W"], wl["H"]
+    outs = [torch.empty((H, W, 4), dtype=torch.float16, device=dev) for _ in wl["frames"]]
+    flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device=dev)  # 256 MiB > 129 MB L2
+
+    def step(evs=None):
+        for i, (az, d_i, d_r) in enumerate(wl["frames"]):
+            if evs is not None:
+                evs[i][0].record(stream)
+            V.vdi_render(vdi, cams[i], W, H, d_i, d_r, outs[i], V.VDI_F16, stream)
+            if evs is not None:
+                evs[i][1].record(stream)
+
+    for i in range(args.warmup):
+        flush.fill_(float(i))
+        step()
+    torch.cuda.synchronize()
+
+    # ---- timed region: K steps, L2 flushed between steps, events per frame
+    evs = [[[torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)]
+            for _ in wl["frames"]] for _ in range(args.steps)]
+    clk = ClockSampler(local_rank)
+    if world > 1:
+        torch.distributed.barrier()
+    torch.cuda.synchronize()
+    for k in range(args.steps):
+        flush.fill_(float(k))
+        step(evs[k])
+    torch.cuda.synchronize()
+    if world > 1:
+        torch.distributed.barrier()
+    clocks = clk.stop()
+    frame_ms = np.array([[evs[k][i][0].elapsed_time(evs[k][i][1]) for i in range(frames_per_step)]
+                         for k in range(args.steps)])
+    step_ms = float(frame_ms.sum(axis=1).mean())
+    if world > 1:
+        tt = torch.tensor([step_ms], device=dev)
+        torch.distributed.all_reduce(tt, op=torch.distributed.ReduceOp.MAX)
+        step_ms = float(tt.item())
+    fps = world * frames_per_step / (step_ms / 1e3)
+    rays = sum((-(-W // d)) * (-(-H // d)) for (_, d, _) in wl["frames"])
+    grays = world * rays / (step_ms / 1e3) / 1e9
+
+    # ---- roofline of the exact-render kernel (frames with d_i = d_r = 1)
+    exact = [i for i, (_, d_i, d_r) in enumerate(wl["frames"]) if d_i == 1 and d_r == 1]
+    touched = [V.touched_bytes(vdi, cams[i], W, H) for i in exact]
+    exact_ms = frame_ms[:, exact].mean(axis=0)
+    achieved = float(np.sum(touched) / (np.sum(exact_ms) / 1e3) / 1e9)
+    peak, peak_src = peaks()
+    traffic = recorded_traffic(args.workload)
+
+    # ---- end to end through the public API: render + read back to pinned host memory
+    host = [torch.empty((H, W, 4), dtype=torch.float16, pin_memory=True) for _ in wl["frames"]]
+    cam_bytes = 2 * 16 * 8
+    e2e_steps = max(3, args.steps // 2)
+    torch.cuda.synchronize()
+    t = time.perf_counter()
+    for k in range(e2e_steps):
+        for i, (az, d_i, d_r) in enumerate(wl["frames"]):
+            V.vdi_render(vdi, V.camera(views[i].view, views[i].proj), W, H, d_i, d_r, outs[i], V.VDI_F16, stream)
+            host[i].copy_(outs[i], non_blocking=True)
+        torch.cuda.synchronize()
+    e2e_s = (time.perf_counter() - t) / e2e_steps
+    e2e = {"value": world * frames_per_step / e2e_s, "unit": "frames/s",
+           "h2d_bytes_per_step": cam_bytes * frames_per_step,
+           "d2h_bytes_per_step": int(sum(o.numel() * o.element_size() for o in outs))}
+
+    launches_per_step = sum(1 if d_i == 1 else 2 for (_, d_i, _) in wl["frames"])
+    result = {
+        "metric": METRIC, "value": fps, "unit": "frames/s", "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": step_ms, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f32", "data": "synthetic", "config": config,
+        "grays_per_s": grays,
+        "frame_ms": {f"{az:g}deg_di{d_i}_dr{d_r}": float(m) for (az, d_i, d_r), m in
+                     zip(wl["frames"], frame_ms.mean(axis=0))},
+        "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                     "frac": achieved / peak, "traffic": traffic, "peak_source": peak_src,
+                     "kernel": "render_kernel (exact path)",
+                     "algorithmic_bytes_per_launch": [int(b) for b in touched]},
+        "clocks": clocks, "e2e": e2e, "gpu_launches": launches_per_step * args.steps,
+        "vdi_generate_ms": gen_s * 1e3, "vdi_bytes": int(layout.depth_bytes + layout.colour_bytes),
+    }
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        try:
+            leg = OracleLeg(wl, vol, bmin, bmax, u, cam_o, views)
+            rng = np.random.default_rng(0)
+            R = leg.rays_for_budget(args.cpu_budget, rng)
+            _, full = leg.run(R, rng)
+            result["cpu_baseline"] = {"value": frames_per_step / full, "unit": "frames/s", "cores": leg.threads,
+                                      "kind": "oracle", "sample": leg.sample_text(R)}
+        except Exception as e:  # the oracle must not take the GPU number down with it
+            result["cpu_baseline"] = {"value": None, "unit": "frames/s", "cores": os.cpu_count(),
+                                      "kind": "oracle", "sample": f"failed: {e}"}
+    V.vdi_destroy(vdi)
+    V.vdi_ctx_destroy(ctx)
+    if rank == 0:
+        print(json.dumps(result))
+    if world > 1:
+        torch.distributed.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

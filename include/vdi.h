@@ -240,6 +240,19 @@ vdi_status vdi_search_first(vdi_t *vdi, int list, int search, const float *d_ent
                             const float *d_exit, const int32_t *seed, const int32_t *increasing,
                             int32_t *result, int n, void *stream);
 
+/* Mark, in a caller-provided zeroed DEVICE bitmap, every 4-byte word of the
+ * VDI's depth and colour arrays that an exact render (d_i = d_r = 1,
+ * Algorithm 2) of `view` at W x H reads under the method's access rule
+ * (Section 4.2: the two depths of the seed probe, one depth per binary-search
+ * probe, front/back depth of each supersegment walked, the colour record of
+ * each supersegment piece composited).  Bit w of word w / 32 stands for byte
+ * offset 4 w of the depth array followed by the colour array; `words` is the
+ * bitmap length in uint32 and must be at least
+ * ceil((depth_bytes + colour_bytes) / 128).  The popcount times 4 is the
+ * number of unique VDI bytes one frame needs (the roofline numerator). */
+vdi_status vdi_touch_bitmap(vdi_t *vdi, const vdi_camera *view, int W, int H, uint32_t *bitmap, size_t words,
+                            void *stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -21,7 +21,7 @@ __all__ = [
     "VDI_F32", "VDI_F16", "VDI_MEM_HOST", "VDI_MEM_DEVICE", "VDI_SEARCH_ALG2", "VDI_SEARCH_BINARY",
     "VDI_SEARCH_LINEAR", "VdiError", "VdiCamera", "VdiDesc", "VdiLayout", "VdiRenderOpts", "load",
     "vdi_ctx_create", "vdi_ctx_destroy", "vdi_layout_bytes", "vdi_create", "vdi_download", "vdi_get_layout",
-    "vdi_destroy", "vdi_render", "vdi_render_ex", "vdi_search_first", "vdi_generate", "camera", "desc",
+    "vdi_destroy", "vdi_render", "vdi_render_ex", "vdi_search_first", "vdi_generate", "vdi_touch_bitmap", "camera", "desc",
 ]
 
 VDI_F32, VDI_F16 = 0, 1
@@ -109,6 +109,7 @@ def load(build_if_needed: bool = True):
     _sig(L, "vdi_render_ex", [P, P, C.c_int, C.c_int, C.c_int, C.c_int, P, C.c_int, P, P])
     _sig(L, "vdi_search_first", [P, C.c_int, C.c_int, P, P, P, P, P, C.c_int, P])
     _sig(L, "vdi_generate", [P, P, P, P, P, C.POINTER(P)])
+    _sig(L, "vdi_touch_bitmap", [P, P, C.c_int, C.c_int, P, C.c_size_t, P])
     _lib = L
     return L
 
@@ -266,3 +267,22 @@ def vdi_generate(ctx, volume, bbox_min, bbox_max, knots, cam_o: VdiCamera, w, h,
     out = P()
     _check(load().vdi_generate(ctx, C.byref(vol), C.byref(tf), C.byref(p), _stream(stream), C.byref(out)))
     return out
+
+
+def vdi_touch_bitmap(vdi, cam: VdiCamera, W, H, bitmap, stream=None):
+    """bitmap: zeroed int32 CUDA tensor with >= ceil((depth_bytes + colour_bytes) / 128) elements."""
+    _check(load().vdi_touch_bitmap(vdi, C.byref(cam), int(W), int(H), _dptr(bitmap), int(bitmap.numel()),
+                                   _stream(stream)))
+
+
+def touched_bytes(vdi, cam: VdiCamera, W, H, stream=None) -> int:
+    """Unique VDI bytes an exact render of this view reads (popcount of the touch bitmap x 4)."""
+    import torch
+
+    L = vdi_get_layout(vdi)
+    words = (L.depth_bytes + L.colour_bytes + 127) // 128
+    bm = torch.zeros(words, dtype=torch.int32, device="cuda")
+    vdi_touch_bitmap(vdi, cam, W, H, bm, stream)
+    torch.cuda.synchronize()
+    b = bm.cpu().numpy().view(np.uint8)
+    return int(np.unpackbits(b).sum()) * 4

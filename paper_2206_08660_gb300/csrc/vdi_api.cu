@@ -20,6 +20,7 @@ namespace vdi {
 
 cudaError_t launch_render(const ViewConsts &c, const DevVdi &v, void *out, int out_fmt, uint32_t *rl,
                           uint32_t *rs, int search, int warp_shape, bool ert, cudaStream_t st);
+cudaError_t launch_touch(const ViewConsts &c, const DevVdi &v, uint32_t *bm, cudaStream_t st);
 cudaError_t launch_upsample(const float4 *lo, int w0, int h0, void *out, int out_fmt, int W, int H,
                             cudaStream_t st);
 cudaError_t launch_search(const DevVdi &v, int li, int search, const float *de, const float *dx,
@@ -513,6 +514,21 @@ VDI_API vdi_status vdi_search_first(vdi_t *v, int list, int search, const float 
     cudaSetDevice(v->ctx->device);
     vdi_status st_ = VDI_OK;
     CK(launch_search(v->dv, list, search, d_entry, d_exit, seed, increasing, result, n, (cudaStream_t)stream));
+done:
+    return st_;
+}
+
+VDI_API vdi_status vdi_touch_bitmap(vdi_t *v, const vdi_camera *view, int W, int H, uint32_t *bitmap, size_t words,
+                                    void *stream) {
+    vdi_status st_ = check_render_args(v, W, H, 1, 1, bitmap, VDI_F32);
+    if (st_ != VDI_OK) return st_;
+    const size_t need = (v->layout.depth_bytes + v->layout.colour_bytes + 127) / 128;
+    if (words < need) return fail(VDI_ERR_INVALID_ARG, "bitmap has %zu words, needs %zu", words, need);
+    cudaSetDevice(v->ctx->device);
+    ViewConsts c;
+    st_ = make_view_consts(v, view, W, H, 1, &c);
+    if (st_ != VDI_OK) return st_;
+    CK(launch_touch(c, v->dv, bitmap, (cudaStream_t)stream));
 done:
     return st_;
 }

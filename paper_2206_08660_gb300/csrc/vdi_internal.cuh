@@ -56,6 +56,32 @@ struct ViewConsts {
     float cell_scale;   // length_unit / (slab view-depth extent * d_r)
 };
 
+// Bytes-touched instrumentation: one bit per 4-byte word of the depth array
+// followed by the colour array.  The marks follow the algorithm's access rule
+// (what a list visit and a supersegment piece need), not the width of the
+// loads that serve it: the seed probe needs the two depths it compares, a
+// binary-search probe one depth, a walked supersegment its front/back depth and
+// its colour record.
+template <bool TOUCH>
+__device__ __forceinline__ void mark_word(uint32_t *bm, size_t w) {
+    if (TOUCH) atomicOr(bm + (w >> 5), 1u << (w & 31));
+}
+template <bool TOUCH>
+__device__ __forceinline__ void mark_depth(const DevVdi &v, uint32_t *bm, int j, int li, int which /*0 f, 1 b*/) {
+    if (TOUCH) mark_word<TOUCH>(bm, ((size_t)(j >> 1) * v.nl + li) * 4 + 2 * (j & 1) + which);
+}
+template <bool TOUCH>
+__device__ __forceinline__ void mark_colour(const DevVdi &v, uint32_t *bm, int j, int li) {
+    if (TOUCH) {
+        const size_t base = (size_t)(v.nsp >> 1) * v.nl * 4;
+        if (v.fmt == 0) {
+            for (int c = 0; c < 4; ++c) mark_word<TOUCH>(bm, base + ((size_t)j * v.nl + li) * 4 + c);
+        } else {
+            for (int c = 0; c < 2; ++c) mark_word<TOUCH>(bm, base + ((size_t)(j >> 1) * v.nl + li) * 4 + 2 * (j & 1) + c);
+        }
+    }
+}
+
 struct PairCache {
     int k;
     float4 d;
@@ -122,14 +148,16 @@ __device__ __forceinline__ float4 get_colour(ColourCache<FMT> &cc, const DevVdi 
 // Depth decreasing along the ray (the ray points back towards V_O): the mirror
 // image, the largest j with f_j <= d_entry (-1 if none), seed q = p & ~1.
 // ---------------------------------------------------------------------------
-template <int MODE>
-__device__ __forceinline__ int first_inc(const DevVdi &v, int li, float d, int p, PairCache &pc) {
+template <int MODE, bool TOUCH = false>
+__device__ __forceinline__ int first_inc(const DevVdi &v, int li, float d, int p, PairCache &pc,
+                                         uint32_t *bm = nullptr) {
     const int nsp = v.nsp;
     if (MODE == kSearchLinear) {
         int j = 0;
         for (; j < nsp; ++j) {
             float f, b;
             get_fb(pc, v, li, j, f, b);
+            mark_depth<TOUCH>(v, bm, j, li, 1);
             if (b >= d) break;
         }
         return j;
@@ -143,6 +171,8 @@ __device__ __forceinline__ int first_inc(const DevVdi &v, int li, float d, int p
             pc.d = ld_depth_pair(v, k, li);
             pc.k = k;
         }
+        mark_depth<TOUCH>(v, bm, q - 1, li, 1);
+        mark_depth<TOUCH>(v, bm, q, li, 1);
         int interval = (pc.d.w >= d) + (pc.d.y >= d);
         if (interval == 1) {
             lo = hi = q;
@@ -156,6 +186,7 @@ __device__ __forceinline__ int first_inc(const DevVdi &v, int li, float d, int p
     }
     while (lo < hi) {  // the single binary search of Algorithm 2 on [lo, hi)
         int mid = (lo + hi) >> 1;
+        mark_depth<TOUCH>(v, bm, mid, li, 1);
         if (ld_back(v, mid, li) >= d)
             hi = mid;
         else
@@ -164,14 +195,16 @@ __device__ __forceinline__ int first_inc(const DevVdi &v, int li, float d, int p
     return lo;
 }
 
-template <int MODE>
-__device__ __forceinline__ int first_dec(const DevVdi &v, int li, float d, int p, PairCache &pc) {
+template <int MODE, bool TOUCH = false>
+__device__ __forceinline__ int first_dec(const DevVdi &v, int li, float d, int p, PairCache &pc,
+                                         uint32_t *bm = nullptr) {
     const int nsp = v.nsp;
     if (MODE == kSearchLinear) {
         int j = -1;
         for (; j + 1 < nsp; ++j) {
             float f, b;
             get_fb(pc, v, li, j + 1, f, b);
+            mark_depth<TOUCH>(v, bm, j + 1, li, 0);
             if (!(f <= d)) break;
         }
         return j;
@@ -185,6 +218,8 @@ __device__ __forceinline__ int first_dec(const DevVdi &v, int li, float d, int p
             pc.d = ld_depth_pair(v, k, li);
             pc.k = k;
         }
+        mark_depth<TOUCH>(v, bm, q, li, 0);
+        mark_depth<TOUCH>(v, bm, q + 1, li, 0);
         int interval = (pc.d.x <= d) + (pc.d.z <= d);
         if (interval == 1) {
             lo = hi = q;
@@ -198,6 +233,7 @@ __device__ __forceinline__ int first_dec(const DevVdi &v, int li, float d, int p
     }
     while (lo < hi) {
         int mid = (lo + hi + 1) >> 1;
+        mark_depth<TOUCH>(v, bm, mid, li, 0);
         if (ld_front(v, mid, li) <= d)
             lo = mid;
         else

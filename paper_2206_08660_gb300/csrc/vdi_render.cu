@@ -105,9 +105,9 @@ __device__ __forceinline__ void add_piece(Accum &acc, float4 col, float len_u) {
 // Exact path: list walk (Amanatides-Woo in V_O NDC), Algorithm 2 per list,
 // adjacency walk over the sorted supersegments, Eq. 2, front-to-back.
 // ---------------------------------------------------------------------------
-template <int FMT, int MODE, bool ERT>
+template <int FMT, int MODE, bool ERT, bool TOUCH = false>
 __device__ __forceinline__ void march_exact(const DevVdi &v, Ray &r, Accum &acc, uint32_t &n_lists,
-                                            uint32_t &n_segs) {
+                                            uint32_t &n_segs, uint32_t *bm = nullptr) {
     const float hw = 0.5f * (float)v.w, hh = 0.5f * (float)v.h;
     const float gx0 = (r.gx0 + 1.f) * hw, gy0 = (1.f - r.gy0) * hh;
     const float dgx = r.dgx * hw, dgy = -r.dgy * hh;
@@ -136,15 +136,18 @@ __device__ __forceinline__ void march_exact(const DevVdi &v, Ray &r, Accum &acc,
             ++n_lists;
             int last = -1, first;
             if (inc) {
-                first = first_inc<MODE>(v, li, d_in, p, pc);
+                first = first_inc<MODE, TOUCH>(v, li, d_in, p, pc, bm);
                 for (int j = first; j < v.nsp; ++j) {
                     float f, b;
                     get_fb(pc, v, li, j, f, b);
+                    mark_depth<TOUCH>(v, bm, j, li, 0);
+                    mark_depth<TOUCH>(v, bm, j, li, 1);
                     if (f > d_out) break;
                     const float sa = (f > d_in) ? fminf(fmaxf((f - z0) * idz, s_in), s_out) : s_in;
                     const float sb = (b < d_out) ? fminf(fmaxf((b - z0) * idz, s_in), s_out) : s_out;
                     last = j;
                     if (sb > sa) {
+                        mark_colour<TOUCH>(v, bm, j, li);
                         const float4 col = get_colour<FMT>(cc, v, li, j);
                         const float da = fmaf(sa, dw, w1), db = fmaf(sb, dw, w1);
                         add_piece(acc, col, lw * (sb - sa) / (da * db));
@@ -154,15 +157,18 @@ __device__ __forceinline__ void march_exact(const DevVdi &v, Ray &r, Accum &acc,
                     if (b > d_out) break;
                 }
             } else {
-                first = first_dec<MODE>(v, li, d_in, p, pc);
+                first = first_dec<MODE, TOUCH>(v, li, d_in, p, pc, bm);
                 for (int j = first; j >= 0; --j) {
                     float f, b;
                     get_fb(pc, v, li, j, f, b);
+                    mark_depth<TOUCH>(v, bm, j, li, 0);
+                    mark_depth<TOUCH>(v, bm, j, li, 1);
                     if (b < d_out) break;
                     const float sa = (b < d_in) ? fminf(fmaxf((b - z0) * idz, s_in), s_out) : s_in;
                     const float sb = (f > d_out) ? fminf(fmaxf((f - z0) * idz, s_in), s_out) : s_out;
                     last = j;
                     if (sb > sa) {
+                        mark_colour<TOUCH>(v, bm, j, li);
                         const float4 col = get_colour<FMT>(cc, v, li, j);
                         const float da = fmaf(sa, dw, w1), db = fmaf(sb, dw, w1);
                         add_piece(acc, col, lw * (sb - sa) / (da * db));
@@ -332,6 +338,27 @@ __global__ void __launch_bounds__(256) render_kernel(const ViewConsts c, const D
     store_px(out, out_fmt, idx, acc);
     if (ray_lists) ray_lists[idx] = nl;
     if (ray_segs) ray_segs[idx] = nsg;
+}
+
+// Instrumented exact render: marks the VDI words the algorithm reads.
+template <int FMT>
+__global__ void __launch_bounds__(256) touch_kernel(const ViewConsts c, const DevVdi v, uint32_t *bm) {
+    int px, py;
+    tile_pixel<32>(px, py);
+    if (px >= c.W || py >= c.H) return;
+    Accum acc = {0.f, 0.f, 0.f, 1.f};
+    uint32_t nl = 0, nsg = 0;
+    Ray r;
+    if (setup_ray(c, px, py, r)) march_exact<FMT, kSearchAlg2, true, true>(v, r, acc, nl, nsg, bm);
+}
+
+cudaError_t launch_touch(const ViewConsts &c, const DevVdi &v, uint32_t *bm, cudaStream_t st) {
+    dim3 grid(div_up(c.W, 32), div_up(c.H, 8)), block(256);
+    if (v.fmt == 0)
+        touch_kernel<0><<<grid, block, 0, st>>>(c, v, bm);
+    else
+        touch_kernel<1><<<grid, block, 0, st>>>(c, v, bm);
+    return cudaGetLastError();
 }
 
 // Bilinear upsampling of the D_I preview: half-pixel centres, clamp to edge.
