@@ -81,7 +81,7 @@ def peaks():
 
 def render_kernel_hash() -> str:
     h = hashlib.sha1()
-    for fn in ("vdi_render.cu", "vdi_internal.cuh"):
+    for fn in ("vdi_render.cu", "vdi_march.cuh", "vdi_internal.cuh"):
         with open(os.path.join(ROOT, "paper_2206_08660_gb300", "csrc", fn), "rb") as f:
             h.update(f.read())
     return h.hexdigest()[:12]
@@ -103,9 +103,10 @@ def recorded_traffic(workload: str):
 
 
 class ClockSampler:
-    """nvidia-smi clocks and throttle reasons sampled every 200 ms."""
+    """nvidia-smi clocks and throttle reasons sampled every 200 ms; only samples
+    taken between mark_start() and mark_stop() are kept."""
 
-    Q = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.hw_slowdown,"
+    Q = ("timestamp,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.hw_slowdown,"
          "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
          "clocks_event_reasons.sw_power_cap")
 
@@ -123,11 +124,23 @@ class ClockSampler:
 
     def _read(self):
         for line in self.proc.stdout:
-            self.lines.append(line.strip())
+            self.lines.append((time.monotonic(), line.strip()))
+
+    def wait_ready(self, timeout=15.0):
+        t = time.monotonic()
+        while self.proc is not None and not self.lines and time.monotonic() - t < timeout:
+            time.sleep(0.05)
+
+    def mark_start(self):
+        self.t0 = time.monotonic()
+
+    def mark_stop(self):
+        self.t1 = time.monotonic()
 
     def stop(self):
         if self.proc is None:
             return None
+        time.sleep(0.25)
         self.proc.terminate()
         try:
             self.proc.wait(timeout=5)
@@ -135,16 +148,19 @@ class ClockSampler:
             self.proc.kill()
         sm, smax, reasons = [], 0.0, set()
         names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
-        for ln in self.lines:
+        t0, t1 = getattr(self, "t0", -1e30), getattr(self, "t1", 1e30)
+        for (ts, ln) in self.lines:
+            if not (t0 - 0.1 <= ts <= t1 + 0.25):
+                continue
             f = [x.strip() for x in ln.split(",")]
-            if len(f) < 7:
+            if len(f) < 8:
                 continue
             try:
-                sm.append(float(f[0]))
-                smax = max(smax, float(f[1]))
+                sm.append(float(f[1]))
+                smax = max(smax, float(f[2]))
             except ValueError:
                 continue
-            for nm, v in zip(names, f[3:7]):
+            for nm, v in zip(names, f[4:8]):
                 if v.lower().startswith("active"):
                     reasons.add(nm)
         if not sm:
@@ -197,8 +213,8 @@ class OracleLeg:
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=20)
-    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--steps", type=int, default=400)
+    ap.add_argument("--warmup", type=int, default=10)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="large", choices=list(WORKLOADS))
     ap.add_argument("--no-cpu-baseline", action="store_true")
@@ -280,6 +296,8 @@ def main():
             if evs is not None:
                 evs[i][1].record(stream)
 
+    clk = ClockSampler(local_rank)  # started before the warm-up so its start-up cost is not timed
+    clk.wait_ready()
     for i in range(args.warmup):
         flush.fill_(float(i))
         step()
@@ -288,14 +306,15 @@ def main():
     # ---- timed region: K steps, L2 flushed between steps, events per frame
     evs = [[[torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)]
             for _ in wl["frames"]] for _ in range(args.steps)]
-    clk = ClockSampler(local_rank)
     if world > 1:
         torch.distributed.barrier()
     torch.cuda.synchronize()
+    clk.mark_start()
     for k in range(args.steps):
         flush.fill_(float(k))
         step(evs[k])
     torch.cuda.synchronize()
+    clk.mark_stop()
     if world > 1:
         torch.distributed.barrier()
     clocks = clk.stop()
@@ -321,7 +340,7 @@ def main():
     # ---- end to end through the public API: render + read back to pinned host memory
     host = [torch.empty((H, W, 4), dtype=torch.float16, pin_memory=True) for _ in wl["frames"]]
     cam_bytes = 2 * 16 * 8
-    e2e_steps = max(3, args.steps // 2)
+    e2e_steps = max(3, min(args.steps, 100))
     torch.cuda.synchronize()
     t = time.perf_counter()
     for k in range(e2e_steps):

@@ -102,6 +102,9 @@ typedef struct {
     uint32_t *ray_lists; /* nullable device [H'][W']: lists traversed with positive length per ray */
     uint32_t *ray_segs;  /* nullable device [H'][W']: supersegment pieces of positive length per ray */
     int warp_shape;      /* -1: default/autotuned; 0: 32x1, 1: 16x2, 2: 8x4 pixels per warp */
+    int no_ess;          /* 1: walk every list the ray crosses (no empty-space skipping, Section 4.3).
+                            The image is the same either way; per-ray counters always come from the
+                            walk over every list. */
 } vdi_render_opts;
 
 /* ---- context ---------------------------------------------------------- */
@@ -184,6 +187,47 @@ vdi_status vdi_render(vdi_t *vdi, const vdi_camera *view, int W, int H, int d_i,
  * the rendered (pre-upsampling) resolution. */
 vdi_status vdi_render_ex(vdi_t *vdi, const vdi_camera *view, int W, int H, int d_i, int d_r,
                          void *out_rgba, int out_fmt, const vdi_render_opts *opts, void *stream);
+
+/* ---- batched multi-view rendering ---------------------------------------
+ * Render up to VDI_BATCH_MAX_REQUESTS views of up to VDI_BATCH_MAX_VDIS
+ * resident VDIs (of any resolutions, formats, previews) in one persistent
+ * launch: every request is cut into 32x8-pixel tiles, and a grid of
+ * (SM count x resident blocks per SM) blocks pulls tiles from one queue.
+ * Each request renders exactly as vdi_render would (the same per-pixel
+ * arithmetic, so results do not depend on what else is in the batch).
+ * With use_graph the launch sequence is replayed from a CUDA graph cached per
+ * batch shape (resolutions, previews, launch configuration, stream); a replay
+ * only updates the graph's kernel parameters.  The graph path keeps its
+ * scratch (tile counter, low-resolution images for D_I > 1) with the cached
+ * graph: batches of one shape on one stream run one after another; the plain
+ * path takes scratch from the stream-ordered allocator.  A cached graph lives
+ * until vdi_ctx_destroy.  warp_shape = -1 uses the configuration stored by
+ * vdi_autotune_batch for batches with the same signature (resolutions,
+ * previews, N_S, colour formats), else 32x1. */
+enum { VDI_BATCH_MAX_REQUESTS = 64, VDI_BATCH_MAX_VDIS = 8 };
+
+typedef struct {
+    vdi_t *vdi;          /* resident VDI (of this context) */
+    vdi_camera view;     /* V_N */
+    int W, H, d_i, d_r;  /* as in vdi_render */
+    void *out;           /* DEVICE [H][W][4] of out_fmt */
+    int out_fmt;
+} vdi_request;
+
+typedef struct {
+    int warp_shape;      /* -1 autotuned/default, 0: 32x1, 1: 16x2, 2: 8x4 pixels per warp */
+    int blocks_per_sm;   /* resident blocks per SM of the persistent grid, 0 = occupancy limit */
+    int use_graph;       /* 1: replay a cached CUDA graph for this batch shape */
+} vdi_batch_opts;
+
+vdi_status vdi_render_batch(vdi_ctx *ctx, const vdi_request *reqs, int n, const vdi_batch_opts *opts, void *stream);
+
+/* Autotuner: time every (warp shape, blocks per SM) on this batch -- it
+ * renders into the requests' outputs -- remember the fastest for batches of
+ * the same signature in this context and return it (with use_graph = 1) and
+ * its time per batch in milliseconds.  Synchronises `stream`. */
+vdi_status vdi_autotune_batch(vdi_ctx *ctx, const vdi_request *reqs, int n, void *stream, vdi_batch_opts *best,
+                              float *best_ms);
 
 /* ---- generation ----------------------------------------------------------
  * Build a VDI from a scalar volume (Section 3) with the homogeneity

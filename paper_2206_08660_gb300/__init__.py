@@ -21,7 +21,8 @@ __all__ = [
     "VDI_F32", "VDI_F16", "VDI_MEM_HOST", "VDI_MEM_DEVICE", "VDI_SEARCH_ALG2", "VDI_SEARCH_BINARY",
     "VDI_SEARCH_LINEAR", "VdiError", "VdiCamera", "VdiDesc", "VdiLayout", "VdiRenderOpts", "load",
     "vdi_ctx_create", "vdi_ctx_destroy", "vdi_layout_bytes", "vdi_create", "vdi_download", "vdi_get_layout",
-    "vdi_destroy", "vdi_render", "vdi_render_ex", "vdi_search_first", "vdi_generate", "vdi_touch_bitmap", "camera", "desc",
+    "vdi_destroy", "vdi_render", "vdi_render_ex", "vdi_search_first", "vdi_generate", "vdi_touch_bitmap", "vdi_render_batch", "vdi_autotune_batch", "request",
+    "VdiRequest", "VdiBatchOpts", "camera", "desc",
 ]
 
 VDI_F32, VDI_F16 = 0, 1
@@ -69,9 +70,18 @@ class VdiGenParams(C.Structure):
                 ("grid_tile", C.c_int), ("grid_nz", C.c_int)]
 
 
+class VdiRequest(C.Structure):
+    _fields_ = [("vdi", C.c_void_p), ("view", VdiCamera), ("W", C.c_int), ("H", C.c_int), ("d_i", C.c_int),
+                ("d_r", C.c_int), ("out", C.c_void_p), ("out_fmt", C.c_int)]
+
+
+class VdiBatchOpts(C.Structure):
+    _fields_ = [("warp_shape", C.c_int), ("blocks_per_sm", C.c_int), ("use_graph", C.c_int)]
+
+
 class VdiRenderOpts(C.Structure):
     _fields_ = [("search", C.c_int), ("no_ert", C.c_int), ("ray_lists", C.c_void_p),
-                ("ray_segs", C.c_void_p), ("warp_shape", C.c_int)]
+                ("ray_segs", C.c_void_p), ("warp_shape", C.c_int), ("no_ess", C.c_int)]
 
 
 _lib = None
@@ -110,6 +120,8 @@ def load(build_if_needed: bool = True):
     _sig(L, "vdi_search_first", [P, C.c_int, C.c_int, P, P, P, P, P, C.c_int, P])
     _sig(L, "vdi_generate", [P, P, P, P, P, C.POINTER(P)])
     _sig(L, "vdi_touch_bitmap", [P, P, C.c_int, C.c_int, P, C.c_size_t, P])
+    _sig(L, "vdi_render_batch", [P, P, C.c_int, P, P])
+    _sig(L, "vdi_autotune_batch", [P, P, C.c_int, P, P, P])
     _lib = L
     return L
 
@@ -231,9 +243,9 @@ def vdi_render(vdi, cam: VdiCamera, W, H, d_i, d_r, out, out_fmt=VDI_F32, stream
 
 
 def vdi_render_ex(vdi, cam: VdiCamera, W, H, d_i, d_r, out, out_fmt=VDI_F32, search=VDI_SEARCH_ALG2,
-                  no_ert=False, ray_lists=None, ray_segs=None, warp_shape=-1, stream=None):
+                  no_ert=False, ray_lists=None, ray_segs=None, warp_shape=-1, no_ess=False, stream=None):
     o = VdiRenderOpts()
-    o.search, o.no_ert, o.warp_shape = int(search), int(bool(no_ert)), int(warp_shape)
+    o.search, o.no_ert, o.warp_shape, o.no_ess = int(search), int(bool(no_ert)), int(warp_shape), int(bool(no_ess))
     o.ray_lists, o.ray_segs = _dptr(ray_lists), _dptr(ray_segs)
     _check(load().vdi_render_ex(vdi, C.byref(cam), int(W), int(H), int(d_i), int(d_r), _dptr(out),
                                 int(out_fmt), C.byref(o), _stream(stream)))
@@ -280,9 +292,39 @@ def touched_bytes(vdi, cam: VdiCamera, W, H, stream=None) -> int:
     import torch
 
     L = vdi_get_layout(vdi)
-    words = (L.depth_bytes + L.colour_bytes + 127) // 128
+    words = (L.depth_bytes + L.colour_bytes + L.grid_bytes + 127) // 128
     bm = torch.zeros(words, dtype=torch.int32, device="cuda")
     vdi_touch_bitmap(vdi, cam, W, H, bm, stream)
     torch.cuda.synchronize()
     b = bm.cpu().numpy().view(np.uint8)
     return int(np.unpackbits(b).sum()) * 4
+
+
+def request(vdi, cam: VdiCamera, W, H, d_i, d_r, out, out_fmt=VDI_F32) -> VdiRequest:
+    r = VdiRequest()
+    r.vdi, r.view, r.W, r.H, r.d_i, r.d_r = vdi, cam, int(W), int(H), int(d_i), int(d_r)
+    r.out, r.out_fmt = _dptr(out), int(out_fmt)
+    return r
+
+
+def _req_array(reqs):
+    arr = (VdiRequest * len(reqs))()
+    for i, r in enumerate(reqs):
+        arr[i] = r
+    return arr
+
+
+def vdi_render_batch(ctx, reqs, warp_shape=-1, blocks_per_sm=0, use_graph=True, stream=None):
+    o = VdiBatchOpts()
+    o.warp_shape, o.blocks_per_sm, o.use_graph = int(warp_shape), int(blocks_per_sm), int(bool(use_graph))
+    arr = _req_array(reqs)
+    _check(load().vdi_render_batch(ctx, arr, len(reqs), C.byref(o), _stream(stream)))
+
+
+def vdi_autotune_batch(ctx, reqs, stream=None):
+    """Returns (VdiBatchOpts of the fastest configuration, milliseconds per batch)."""
+    best = VdiBatchOpts()
+    ms = C.c_float()
+    arr = _req_array(reqs)
+    _check(load().vdi_autotune_batch(ctx, arr, len(reqs), _stream(stream), C.byref(best), C.byref(ms)))
+    return best, ms.value

@@ -19,7 +19,7 @@
 namespace vdi {
 
 cudaError_t launch_render(const ViewConsts &c, const DevVdi &v, void *out, int out_fmt, uint32_t *rl,
-                          uint32_t *rs, int search, int warp_shape, bool ert, cudaStream_t st);
+                          uint32_t *rs, int search, int warp_shape, bool ert, bool ess, cudaStream_t st);
 cudaError_t launch_touch(const ViewConsts &c, const DevVdi &v, uint32_t *bm, cudaStream_t st);
 cudaError_t launch_upsample(const float4 *lo, int w0, int h0, void *out, int out_fmt, int W, int H,
                             cudaStream_t st);
@@ -290,7 +290,12 @@ VDI_API vdi_status vdi_ctx_create(int device, vdi_ctx **out) {
     return VDI_OK;
 }
 
-VDI_API void vdi_ctx_destroy(vdi_ctx *ctx) { delete ctx; }
+VDI_API void vdi_ctx_destroy(vdi_ctx *ctx) {
+    if (!ctx) return;
+    cudaSetDevice(ctx->device);
+    release_batch_cache(ctx);
+    delete ctx;
+}
 
 VDI_API vdi_status vdi_layout_bytes(const vdi_desc *desc, vdi_layout *out) {
     if (!out) return fail(VDI_ERR_INVALID_ARG, "out is NULL");
@@ -474,7 +479,7 @@ VDI_API vdi_status vdi_render_ex(vdi_t *v, const vdi_camera *view, int W, int H,
                                  void *out_rgba, int out_fmt, const vdi_render_opts *opts, void *stream) {
     vdi_status st_ = check_render_args(v, W, H, d_i, d_r, out_rgba, out_fmt);
     if (st_ != VDI_OK) return st_;
-    vdi_render_opts o = {VDI_SEARCH_ALG2, 0, nullptr, nullptr, -1};
+    vdi_render_opts o = {VDI_SEARCH_ALG2, 0, nullptr, nullptr, -1, 0};
     if (opts) o = *opts;
     if (o.search < 0 || o.search > 2) return fail(VDI_ERR_INVALID_ARG, "search=%d", o.search);
     if (o.warp_shape < -1 || o.warp_shape > 2) return fail(VDI_ERR_INVALID_ARG, "warp_shape=%d", o.warp_shape);
@@ -487,10 +492,11 @@ VDI_API vdi_status vdi_render_ex(vdi_t *v, const vdi_camera *view, int W, int H,
     const int ws = o.warp_shape >= 0 ? o.warp_shape : default_warp_shape(v, Wr, Hr);
     float4 *lo = nullptr;
     if (d_i == 1) {
-        CK(launch_render(c, v->dv, out_rgba, out_fmt, o.ray_lists, o.ray_segs, o.search, ws, !o.no_ert, st));
+        CK(launch_render(c, v->dv, out_rgba, out_fmt, o.ray_lists, o.ray_segs, o.search, ws, !o.no_ert, !o.no_ess,
+                         st));
     } else {
         CK(cudaMallocAsync((void **)&lo, (size_t)Wr * Hr * sizeof(float4), st));
-        CK(launch_render(c, v->dv, lo, VDI_F32, o.ray_lists, o.ray_segs, o.search, ws, !o.no_ert, st));
+        CK(launch_render(c, v->dv, lo, VDI_F32, o.ray_lists, o.ray_segs, o.search, ws, !o.no_ert, !o.no_ess, st));
         CK(launch_upsample(lo, Wr, Hr, out_rgba, out_fmt, W, H, st));
     }
 done:
@@ -522,7 +528,7 @@ VDI_API vdi_status vdi_touch_bitmap(vdi_t *v, const vdi_camera *view, int W, int
                                     void *stream) {
     vdi_status st_ = check_render_args(v, W, H, 1, 1, bitmap, VDI_F32);
     if (st_ != VDI_OK) return st_;
-    const size_t need = (v->layout.depth_bytes + v->layout.colour_bytes + 127) / 128;
+    const size_t need = (v->layout.depth_bytes + v->layout.colour_bytes + v->layout.grid_bytes + 127) / 128;
     if (words < need) return fail(VDI_ERR_INVALID_ARG, "bitmap has %zu words, needs %zu", words, need);
     cudaSetDevice(v->ctx->device);
     ViewConsts c;

@@ -35,6 +35,8 @@ void mat4_mul(const double *A, const double *B, double *C);
 bool mat4_inv(const double *m, double *out);
 double ndc_to_view_depth(const double *P, double Z);
 void grid_edges(const double *P, int nz, float *edges);
+vdi_status check_render_args(const vdi_t *v, int W, int H, int d_i, int d_r, const void *out, int out_fmt);
+void release_batch_cache(vdi_ctx *ctx);
 
 // warp shape used when the caller does not choose one: 32x1 (lanes along a
 // row of lists) unless the autotuner recorded a better one

@@ -202,3 +202,21 @@ def test_invalid_inputs_are_reported(V, ctx):
                 V.vdi_render(vdi, V.camera(cam.view, cam.proj), args[0], args[1], args[2], args[3], out)
     finally:
         V.vdi_destroy(vdi)
+
+
+@pytest.mark.parametrize("fmt", [0, 1])
+def test_empty_space_skipping_changes_nothing(V, ctx, fmt):
+    """Section 4.3: cells whose count is 0 hold no supersegment, so skipping them
+    leaves the image unchanged (up to the rounding of splitting a supersegment
+    piece at cell boundaries)."""
+    for seed, fill in ((4, 0.3), (5, 0.9)):
+        case = random_case(96, 64, 6, seed=seed, fill=fill)
+        vdi = V.vdi_create(ctx, case.gpu_desc(V, fmt, T=8, nz=16), case.vdi.rgba, case.vdi.depth, case.vdi.counts)
+        try:
+            for (az, el, zoom, ortho) in VIEWS:
+                cn = S.orbit_camera(case.bmin, case.bmax, 1.25, az_deg=az, el_deg=el, zoom=zoom, ortho=ortho)
+                a = gpu_render(V, vdi, cn, 80, 64)
+                b = gpu_render(V, vdi, cn, 80, 64, no_ess=True)
+                assert np.abs(a - b).max() < 2e-5, (seed, az)
+        finally:
+            V.vdi_destroy(vdi)
