@@ -90,6 +90,7 @@ typedef struct {
     size_t depth_bytes;  /* front/back FP32 depths on the device */
     size_t colour_bytes; /* colour + opacity on the device */
     size_t grid_bytes;   /* uint32 supersegment counts */
+    size_t list_bytes;   /* per list: front of its first and back of its last supersegment (float2) */
     size_t total_bytes;  /* everything the VDI holds on the device */
     size_t paper_bytes;  /* size in the paper's RGBA32F + 2 x R32F layout: 24 B per slot (Section 5) */
     int grid_w, grid_h, grid_nz;
@@ -228,6 +229,72 @@ vdi_status vdi_render_batch(vdi_ctx *ctx, const vdi_request *reqs, int n, const 
  * its time per batch in milliseconds.  Synchronises `stream`. */
 vdi_status vdi_autotune_batch(vdi_ctx *ctx, const vdi_request *reqs, int n, void *stream, vdi_batch_opts *best,
                               float *best_ms);
+
+/* ---- serving ---------------------------------------------------------------
+ * A continuous-batching view server over resident VDIs.  The paper's client
+ * renders views from the resident VDI while the next one is uploaded in the
+ * background (Section 5, double buffering); here up to n_slots VDIs stay
+ * resident and any number of clients submit view requests:
+ *  - vdi_server_submit queues a request and returns a ticket at once;
+ *  - a scheduler thread admits queued requests FIFO into the next batch as
+ *    soon as one of `max_inflight` batch streams is free and their image
+ *    memory (plus low-resolution scratch for D_I > 1) fits under
+ *    `budget_bytes` next to everything not yet released; a request that can
+ *    never fit fails with VDI_ERR_OOM; batches run while new requests are
+ *    admitted behind them (continuous batching, work overlaps on the device);
+ *  - each batch is one vdi_render_batch launch: every result equals the same
+ *    view rendered alone by vdi_render;
+ *  - vdi_server_set_vdi installs or replaces a slot's VDI at any time (the
+ *    server takes ownership).  Batches formed after the work enqueued on
+ *    `ready_stream` (e.g. the side stream of a vdi_generate) has completed use
+ *    the new VDI; the old one is freed when the last batch using it retires;
+ *  - results stay in server-owned DEVICE memory until vdi_server_release;
+ *  - waits are bounded: vdi_server_wait returns VDI_ERR_TIMEOUT.
+ * Times are seconds of a host monotonic clock. */
+typedef struct vdi_server vdi_server;
+
+typedef struct {
+    size_t budget_bytes;   /* device memory for unreleased results and preview scratch */
+    int max_batch;         /* requests per launch, 1..VDI_BATCH_MAX_REQUESTS */
+    int max_inflight;      /* batches on the device at once (streams), 1..16 */
+    int n_slots;           /* resident VDI slots, 1..VDI_BATCH_MAX_VDIS */
+    double wait_timeout_s; /* bound on internal waits at shutdown (0 -> 10 s) */
+} vdi_server_config;
+
+typedef struct {
+    int slot;              /* resident VDI slot */
+    vdi_camera view;
+    int W, H, d_i, d_r, out_fmt;
+} vdi_view_request;
+
+typedef struct {
+    int status;            /* -1 while queued or running, else a vdi_status */
+    double t_submit, t_start, t_done;
+    void *image;           /* DEVICE [H][W][4] of out_fmt when status == VDI_OK */
+    size_t image_bytes;
+} vdi_ticket_info;
+
+typedef struct {
+    uint64_t submitted, completed, failed, batches, batched_requests, vdi_installs;
+    uint64_t pending, batches_in_flight;
+    size_t bytes_in_use;
+} vdi_server_counters;
+
+vdi_status vdi_server_create(vdi_ctx *ctx, const vdi_server_config *cfg, vdi_server **out);
+vdi_status vdi_server_set_vdi(vdi_server *s, int slot, vdi_t *vdi, void *ready_stream);
+vdi_status vdi_server_submit(vdi_server *s, const vdi_view_request *req, uint64_t *ticket);
+vdi_status vdi_server_wait(vdi_server *s, uint64_t ticket, double timeout_s, vdi_ticket_info *info);
+vdi_status vdi_server_poll(vdi_server *s, uint64_t ticket, vdi_ticket_info *info);
+/* Copy a finished ticket's image into the caller's buffer (`dst_kind` is
+ * VDI_MEM_HOST or VDI_MEM_DEVICE; `bytes` must equal the image size), ordered
+ * on `stream` and synchronised before returning. */
+vdi_status vdi_server_read(vdi_server *s, uint64_t ticket, void *dst, size_t bytes, int dst_kind, void *stream);
+/* Free a finished ticket's result (VDI_ERR_BUSY while it is still running). */
+vdi_status vdi_server_release(vdi_server *s, uint64_t ticket);
+vdi_status vdi_server_stats(vdi_server *s, vdi_server_counters *out);
+/* Stops admitting, waits (bounded) for batches in flight, frees everything
+ * including the installed VDIs. */
+void vdi_server_destroy(vdi_server *s);
 
 /* ---- generation ----------------------------------------------------------
  * Build a VDI from a scalar volume (Section 3) with the homogeneity

@@ -22,6 +22,8 @@ __all__ = [
     "VDI_SEARCH_LINEAR", "VdiError", "VdiCamera", "VdiDesc", "VdiLayout", "VdiRenderOpts", "load",
     "vdi_ctx_create", "vdi_ctx_destroy", "vdi_layout_bytes", "vdi_create", "vdi_download", "vdi_get_layout",
     "vdi_destroy", "vdi_render", "vdi_render_ex", "vdi_search_first", "vdi_generate", "vdi_touch_bitmap", "vdi_render_batch", "vdi_autotune_batch", "request",
+    "vdi_server_create", "vdi_server_set_vdi", "vdi_server_submit", "vdi_server_wait", "vdi_server_poll",
+    "vdi_server_release", "vdi_server_read", "vdi_server_stats", "vdi_server_destroy", "VdiViewRequest", "VdiTicketInfo",
     "VdiRequest", "VdiBatchOpts", "camera", "desc",
 ]
 
@@ -51,7 +53,7 @@ class VdiDesc(C.Structure):
 
 class VdiLayout(C.Structure):
     _fields_ = [("depth_bytes", C.c_size_t), ("colour_bytes", C.c_size_t), ("grid_bytes", C.c_size_t),
-                ("total_bytes", C.c_size_t), ("paper_bytes", C.c_size_t), ("grid_w", C.c_int),
+                ("list_bytes", C.c_size_t), ("total_bytes", C.c_size_t), ("paper_bytes", C.c_size_t), ("grid_w", C.c_int),
                 ("grid_h", C.c_int), ("grid_nz", C.c_int), ("n_s_stored", C.c_int)]
 
 
@@ -77,6 +79,27 @@ class VdiRequest(C.Structure):
 
 class VdiBatchOpts(C.Structure):
     _fields_ = [("warp_shape", C.c_int), ("blocks_per_sm", C.c_int), ("use_graph", C.c_int)]
+
+
+class VdiServerConfig(C.Structure):
+    _fields_ = [("budget_bytes", C.c_size_t), ("max_batch", C.c_int), ("max_inflight", C.c_int),
+                ("n_slots", C.c_int), ("wait_timeout_s", C.c_double)]
+
+
+class VdiViewRequest(C.Structure):
+    _fields_ = [("slot", C.c_int), ("view", VdiCamera), ("W", C.c_int), ("H", C.c_int), ("d_i", C.c_int),
+                ("d_r", C.c_int), ("out_fmt", C.c_int)]
+
+
+class VdiTicketInfo(C.Structure):
+    _fields_ = [("status", C.c_int), ("t_submit", C.c_double), ("t_start", C.c_double), ("t_done", C.c_double),
+                ("image", C.c_void_p), ("image_bytes", C.c_size_t)]
+
+
+class VdiServerCounters(C.Structure):
+    _fields_ = [("submitted", C.c_uint64), ("completed", C.c_uint64), ("failed", C.c_uint64),
+                ("batches", C.c_uint64), ("batched_requests", C.c_uint64), ("vdi_installs", C.c_uint64),
+                ("pending", C.c_uint64), ("batches_in_flight", C.c_uint64), ("bytes_in_use", C.c_size_t)]
 
 
 class VdiRenderOpts(C.Structure):
@@ -122,6 +145,15 @@ def load(build_if_needed: bool = True):
     _sig(L, "vdi_touch_bitmap", [P, P, C.c_int, C.c_int, P, C.c_size_t, P])
     _sig(L, "vdi_render_batch", [P, P, C.c_int, P, P])
     _sig(L, "vdi_autotune_batch", [P, P, C.c_int, P, P, P])
+    _sig(L, "vdi_server_create", [P, P, C.POINTER(P)])
+    _sig(L, "vdi_server_set_vdi", [P, C.c_int, P, P])
+    _sig(L, "vdi_server_submit", [P, P, C.POINTER(C.c_uint64)])
+    _sig(L, "vdi_server_wait", [P, C.c_uint64, C.c_double, P])
+    _sig(L, "vdi_server_poll", [P, C.c_uint64, P])
+    _sig(L, "vdi_server_release", [P, C.c_uint64])
+    _sig(L, "vdi_server_read", [P, C.c_uint64, P, C.c_size_t, C.c_int, P])
+    _sig(L, "vdi_server_stats", [P, P])
+    _sig(L, "vdi_server_destroy", [P], None)
     _lib = L
     return L
 
@@ -292,7 +324,8 @@ def touched_bytes(vdi, cam: VdiCamera, W, H, stream=None) -> int:
     import torch
 
     L = vdi_get_layout(vdi)
-    words = (L.depth_bytes + L.colour_bytes + L.grid_bytes + 127) // 128
+    grid_words = (L.grid_w * L.grid_h * L.grid_nz + 3) // 4 * 4
+    words = ((L.depth_bytes + L.colour_bytes) // 4 + grid_words + L.list_bytes // 4 + 31) // 32
     bm = torch.zeros(words, dtype=torch.int32, device="cuda")
     vdi_touch_bitmap(vdi, cam, W, H, bm, stream)
     torch.cuda.synchronize()
@@ -328,3 +361,65 @@ def vdi_autotune_batch(ctx, reqs, stream=None):
     arr = _req_array(reqs)
     _check(load().vdi_autotune_batch(ctx, arr, len(reqs), _stream(stream), C.byref(best), C.byref(ms)))
     return best, ms.value
+
+
+def vdi_server_create(ctx, budget_bytes, max_batch=32, max_inflight=2, n_slots=8, wait_timeout_s=10.0):
+    c = VdiServerConfig()
+    c.budget_bytes, c.max_batch, c.max_inflight = int(budget_bytes), int(max_batch), int(max_inflight)
+    c.n_slots, c.wait_timeout_s = int(n_slots), float(wait_timeout_s)
+    out = P()
+    _check(load().vdi_server_create(ctx, C.byref(c), C.byref(out)))
+    return out
+
+
+def vdi_server_set_vdi(server, slot, vdi, ready_stream=None):
+    """Install or replace the VDI of a slot; the server takes ownership of `vdi`."""
+    _check(load().vdi_server_set_vdi(server, int(slot), vdi, _stream(ready_stream)))
+
+
+def view_request(slot, cam: VdiCamera, W, H, d_i=1, d_r=1, out_fmt=VDI_F16) -> VdiViewRequest:
+    r = VdiViewRequest()
+    r.slot, r.view, r.W, r.H, r.d_i, r.d_r, r.out_fmt = int(slot), cam, int(W), int(H), int(d_i), int(d_r), \
+        int(out_fmt)
+    return r
+
+
+def vdi_server_submit(server, req: VdiViewRequest) -> int:
+    t = C.c_uint64()
+    _check(load().vdi_server_submit(server, C.byref(req), C.byref(t)))
+    return t.value
+
+
+def vdi_server_wait(server, ticket, timeout_s=10.0) -> VdiTicketInfo:
+    info = VdiTicketInfo()
+    _check(load().vdi_server_wait(server, C.c_uint64(ticket), float(timeout_s), C.byref(info)))
+    return info
+
+
+def vdi_server_poll(server, ticket) -> VdiTicketInfo:
+    info = VdiTicketInfo()
+    _check(load().vdi_server_poll(server, C.c_uint64(ticket), C.byref(info)))
+    return info
+
+
+def vdi_server_read(server, ticket, dst, stream=None):
+    """Copy a finished result into `dst` (numpy array -> host copy, CUDA tensor -> device copy)."""
+    if isinstance(dst, np.ndarray):
+        ptr, kind, n = dst.ctypes.data, VDI_MEM_HOST, dst.nbytes
+    else:
+        ptr, kind, n = _dptr(dst), VDI_MEM_DEVICE, dst.numel() * dst.element_size()
+    _check(load().vdi_server_read(server, C.c_uint64(ticket), ptr, n, kind, _stream(stream)))
+
+
+def vdi_server_release(server, ticket):
+    _check(load().vdi_server_release(server, C.c_uint64(ticket)))
+
+
+def vdi_server_stats(server) -> VdiServerCounters:
+    st = VdiServerCounters()
+    _check(load().vdi_server_stats(server, C.byref(st)))
+    return st
+
+
+def vdi_server_destroy(server):
+    load().vdi_server_destroy(server)

@@ -29,6 +29,8 @@ cudaError_t launch_count_leading(const float *depth, int ns, long long nl, int32
 cudaError_t launch_convert(int fmt, const float *rgba, const float *depth, const int32_t *counts, int ns,
                            int nsp, long long nl, float4 *dpair, void *colour, unsigned *err, cudaStream_t st);
 cudaError_t launch_grid(const DevVdi &v, uint32_t *grid, cudaStream_t st);
+cudaError_t launch_range(const float *depth, const int32_t *counts, int ns, long long nl, float2 *range,
+                         cudaStream_t st);
 cudaError_t launch_download(const DevVdi &v, int ns, float *rgba, float *depth, int32_t *counts,
                             cudaStream_t st);
 
@@ -132,7 +134,8 @@ vdi_status check_desc(const vdi_desc *d, vdi_layout *L) {
     L->grid_h = div_up(d->h, T);
     L->grid_nz = nz;
     L->grid_bytes = (size_t)L->grid_w * L->grid_h * nz * sizeof(uint32_t);
-    L->total_bytes = L->depth_bytes + L->colour_bytes + L->grid_bytes;
+    L->list_bytes = nl * 2 * sizeof(float);
+    L->total_bytes = L->depth_bytes + L->colour_bytes + L->grid_bytes + L->list_bytes;
     L->paper_bytes = nl * (size_t)d->n_s * 24;
     return VDI_OK;
 }
@@ -286,6 +289,17 @@ VDI_API vdi_status vdi_ctx_create(int device, vdi_ctx **out) {
     if (!c) return fail(VDI_ERR_OOM, "host allocation");
     c->device = device;
     cudaDeviceGetAttribute(&c->sm_count, cudaDevAttrMultiProcessorCount, device);
+    if ((e = cudaStreamCreateWithFlags(&c->free_stream, cudaStreamNonBlocking)) != cudaSuccess) {
+        delete c;
+        return cuda_fail(e, "cudaStreamCreate");
+    }
+    // VDIs and server images come from the stream-ordered allocator; keep freed
+    // blocks in the pool instead of returning them to the driver at every sync
+    cudaMemPool_t pool;
+    if (cudaDeviceGetDefaultMemPool(&pool, device) == cudaSuccess) {
+        uint64_t thr = UINT64_MAX;
+        cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &thr);
+    }
     *out = c;
     return VDI_OK;
 }
@@ -294,6 +308,10 @@ VDI_API void vdi_ctx_destroy(vdi_ctx *ctx) {
     if (!ctx) return;
     cudaSetDevice(ctx->device);
     release_batch_cache(ctx);
+    if (ctx->free_stream) {
+        cudaStreamSynchronize(ctx->free_stream);
+        cudaStreamDestroy(ctx->free_stream);
+    }
     delete ctx;
 }
 
@@ -319,7 +337,7 @@ VDI_API vdi_status vdi_get_layout(const vdi_t *v, vdi_layout *out) {
 
 namespace vdi {
 
-vdi_status alloc_vdi(vdi_ctx *ctx, const vdi_desc *desc, vdi_t **out) {
+vdi_status alloc_vdi(vdi_ctx *ctx, const vdi_desc *desc, cudaStream_t stream, vdi_t **out) {
     vdi_layout L;
     vdi_status s = check_desc(desc, &L);
     if (s != VDI_OK) return s;
@@ -350,28 +368,37 @@ vdi_status alloc_vdi(vdi_ctx *ctx, const vdi_desc *desc, vdi_t **out) {
     d.nz = L.grid_nz;
     grid_edges(desc->orig.proj, d.nz, d.edges);
     cudaError_t e;
-    if ((e = cudaMalloc(&v->depth_mem, L.depth_bytes)) != cudaSuccess ||
-        (e = cudaMalloc(&v->colour_mem, L.colour_bytes)) != cudaSuccess ||
-        (e = cudaMalloc(&v->grid_mem, L.grid_bytes)) != cudaSuccess) {
-        cudaFree(v->depth_mem);
-        cudaFree(v->colour_mem);
-        cudaFree(v->grid_mem);
+    if ((e = cudaMallocAsync(&v->depth_mem, L.depth_bytes, stream)) != cudaSuccess ||
+        (e = cudaMallocAsync(&v->colour_mem, L.colour_bytes, stream)) != cudaSuccess ||
+        (e = cudaMallocAsync((void **)&v->grid_mem, L.grid_bytes, stream)) != cudaSuccess ||
+        (e = cudaMallocAsync((void **)&v->range_mem, L.list_bytes, stream)) != cudaSuccess) {
+        vdi_status r = cuda_fail(e, "cudaMallocAsync(VDI)");
+        if (v->depth_mem) cudaFreeAsync(v->depth_mem, stream);
+        if (v->colour_mem) cudaFreeAsync(v->colour_mem, stream);
+        if (v->grid_mem) cudaFreeAsync(v->grid_mem, stream);
+        if (v->range_mem) cudaFreeAsync(v->range_mem, stream);
         delete v;
-        return cuda_fail(e, "cudaMalloc(VDI)");
+        return r;
     }
     d.depth = reinterpret_cast<const float4 *>(v->depth_mem);
     d.colour = v->colour_mem;
     d.grid = v->grid_mem;
+    d.range = v->range_mem;
     *out = v;
     return VDI_OK;
 }
 
+// Stream-ordered free on the context's free stream: the caller guarantees
+// that no work still reads the VDI (vdi_destroy synchronises the device
+// first; the server frees a VDI version only after its last batch retired).
 void free_vdi(vdi_t *v) {
     if (!v) return;
     cudaSetDevice(v->ctx->device);
-    cudaFree(v->depth_mem);
-    cudaFree(v->colour_mem);
-    cudaFree(v->grid_mem);
+    cudaStream_t fs = v->ctx->free_stream;
+    if (v->depth_mem) cudaFreeAsync(v->depth_mem, fs);
+    if (v->colour_mem) cudaFreeAsync(v->colour_mem, fs);
+    if (v->grid_mem) cudaFreeAsync(v->grid_mem, fs);
+    if (v->range_mem) cudaFreeAsync(v->range_mem, fs);
     delete v;
 }
 
@@ -385,7 +412,7 @@ VDI_API vdi_status vdi_create(vdi_ctx *ctx, const vdi_desc *desc, const float *r
     cudaSetDevice(ctx->device);
     cudaStream_t st = (cudaStream_t)stream;
     vdi_t *v = nullptr;
-    vdi_status st_ = alloc_vdi(ctx, desc, &v);
+    vdi_status st_ = alloc_vdi(ctx, desc, st, &v);
     if (st_ != VDI_OK) return st_;
     const size_t nl = (size_t)desc->w * desc->h, nslot = nl * desc->n_s;
     float *d_rgba = nullptr, *d_depth = nullptr;
@@ -412,6 +439,7 @@ VDI_API vdi_status vdi_create(vdi_ctx *ctx, const vdi_desc *desc, const float *r
     CK(launch_convert(desc->colour_fmt, d_rgba, d_depth, d_counts, desc->n_s, v->dv.nsp, (long long)nl,
                       reinterpret_cast<float4 *>(v->depth_mem), v->colour_mem, d_err, st));
     CK(launch_grid(v->dv, v->grid_mem, st));
+    CK(launch_range(d_depth, d_counts, desc->n_s, (long long)nl, v->range_mem, st));
     CK(cudaMemcpyAsync(&h_err, d_err, sizeof(unsigned), cudaMemcpyDeviceToHost, st));
     CK(cudaStreamSynchronize(st));
     if (h_err & 1u)
@@ -460,9 +488,21 @@ done:
     return st_;
 }
 
-VDI_API void vdi_destroy(vdi_t *v) { free_vdi(v); }
+VDI_API void vdi_destroy(vdi_t *v) {
+    if (!v) return;
+    cudaSetDevice(v->ctx->device);
+    cudaDeviceSynchronize();  // work still reading the VDI on any stream completes first
+    free_vdi(v);
+}
 
 namespace vdi {
+
+// length in uint32 of the touch bitmap: depth, colour, grid padded to 16 bytes, list ranges
+size_t touch_words(const vdi_t *v) {
+    const size_t grid_words = ((size_t)v->dv.nz * v->dv.gh * v->dv.gw + 3) & ~(size_t)3;
+    const size_t words = (v->layout.depth_bytes + v->layout.colour_bytes) / 4 + grid_words + v->layout.list_bytes / 4;
+    return (words + 31) / 32;
+}
 
 vdi_status check_render_args(const vdi_t *v, int W, int H, int d_i, int d_r, const void *out, int out_fmt) {
     if (!v) return fail(VDI_ERR_INVALID_ARG, "vdi is NULL");
@@ -528,7 +568,7 @@ VDI_API vdi_status vdi_touch_bitmap(vdi_t *v, const vdi_camera *view, int W, int
                                     void *stream) {
     vdi_status st_ = check_render_args(v, W, H, 1, 1, bitmap, VDI_F32);
     if (st_ != VDI_OK) return st_;
-    const size_t need = (v->layout.depth_bytes + v->layout.colour_bytes + v->layout.grid_bytes + 127) / 128;
+    const size_t need = touch_words(v);
     if (words < need) return fail(VDI_ERR_INVALID_ARG, "bitmap has %zu words, needs %zu", words, need);
     cudaSetDevice(v->ctx->device);
     ViewConsts c;

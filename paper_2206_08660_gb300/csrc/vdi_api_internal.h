@@ -9,6 +9,7 @@
 struct vdi_ctx {
     int device = 0;
     int sm_count = 0;
+    cudaStream_t free_stream = nullptr;  // stream-ordered frees of VDI memory
 };
 
 struct vdi_t {
@@ -21,6 +22,7 @@ struct vdi_t {
     void *depth_mem = nullptr;
     void *colour_mem = nullptr;
     uint32_t *grid_mem = nullptr;
+    float2 *range_mem = nullptr;
 };
 
 namespace vdi {
@@ -29,12 +31,13 @@ vdi_status fail(vdi_status s, const char *fmt, ...);
 vdi_status cuda_fail(cudaError_t e, const char *what);
 vdi_status check_desc(const vdi_desc *d, vdi_layout *L);
 vdi_status make_view_consts(const vdi_t *v, const vdi_camera *cam, int W, int H, int d_r, ViewConsts *c);
-vdi_status alloc_vdi(vdi_ctx *ctx, const vdi_desc *desc, vdi_t **out);
+vdi_status alloc_vdi(vdi_ctx *ctx, const vdi_desc *desc, cudaStream_t stream, vdi_t **out);
 void free_vdi(vdi_t *v);
 void mat4_mul(const double *A, const double *B, double *C);
 bool mat4_inv(const double *m, double *out);
 double ndc_to_view_depth(const double *P, double Z);
 void grid_edges(const double *P, int nz, float *edges);
+size_t touch_words(const vdi_t *v);
 vdi_status check_render_args(const vdi_t *v, int W, int H, int d_i, int d_r, const void *out, int out_fmt);
 void release_batch_cache(vdi_ctx *ctx);
 

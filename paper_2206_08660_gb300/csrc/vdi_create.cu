@@ -121,6 +121,16 @@ __global__ void grid_kernel(const DevVdi v, uint32_t *__restrict__ grid) {
         grid[((size_t)z * v.gh + cy) * v.gw + cx] = cnt[z];
 }
 
+// Per list: front of the first and back of the last valid supersegment.
+__global__ void range_kernel(const float *__restrict__ depth, const int32_t *__restrict__ counts, int ns,
+                             long long nl, float2 *__restrict__ range) {
+    const long long li = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (li >= nl) return;
+    const int n = min(max(counts[li], 0), ns);
+    range[li] = n ? make_float2(depth[(size_t)li * ns * 2], depth[((size_t)li * ns + n - 1) * 2 + 1])
+                  : make_float2(INFINITY, -INFINITY);
+}
+
 // Device layout -> array-of-structures (premultiplied rgba, alpha per unit).
 template <int FMT>
 __global__ void download_kernel(const DevVdi v, int ns, float *__restrict__ rgba, float *__restrict__ depth,
@@ -170,6 +180,12 @@ cudaError_t launch_convert(int fmt, const float *rgba, const float *depth, const
 cudaError_t launch_grid(const DevVdi &v, uint32_t *grid, cudaStream_t st) {
     dim3 g(v.gw, v.gh);
     grid_kernel<<<g, 256, 0, st>>>(v, grid);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_range(const float *depth, const int32_t *counts, int ns, long long nl, float2 *range,
+                         cudaStream_t st) {
+    range_kernel<<<(unsigned)((nl + 255) / 256), 256, 0, st>>>(depth, counts, ns, nl, range);
     return cudaGetLastError();
 }
 

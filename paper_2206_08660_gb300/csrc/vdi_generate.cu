@@ -118,7 +118,7 @@ __device__ __forceinline__ void write_pair(const GenConsts &g, float4 *depth, vo
 }
 
 __global__ void __launch_bounds__(256) generate_kernel(const GenConsts g, float4 *__restrict__ depth,
-                                                       void *__restrict__ colour) {
+                                                       void *__restrict__ colour, float2 *__restrict__ range) {
     const int px = blockIdx.x * 32 + (threadIdx.x & 31);
     const int py = blockIdx.y * 8 + (threadIdx.x >> 5);
     if (px >= g.w || py >= g.h) return;
@@ -128,7 +128,10 @@ __global__ void __launch_bounds__(256) generate_kernel(const GenConsts g, float4
     sw.pf = sw.pb = INFINITY;
     sw.pc = make_float4(0.f, 0.f, 0.f, 0.f);
 
+    float first_f = INFINITY, last_b = -INFINITY;
     auto emit = [&](float f, float b, float4 col) {
+        if (sw.nseg == 0) first_f = f;
+        last_b = b;
         const int j = sw.nseg++;
         if ((j & 1) == 0) {
             sw.pf = f;
@@ -239,6 +242,7 @@ __global__ void __launch_bounds__(256) generate_kernel(const GenConsts g, float4
     }
     for (; j < g.nsp; j += 2)
         write_pair(g, depth, colour, li, j >> 1, INFINITY, INFINITY, zero, INFINITY, INFINITY, zero);
+    range[li] = make_float2(first_f, last_b);
 }
 
 #undef ADD
@@ -301,7 +305,7 @@ VDI_API vdi_status vdi_generate(vdi_ctx *ctx, const vdi_volume *vol, const vdi_t
     if (!mat4_inv(prm->orig.view, Vi)) return fail(VDI_ERR_INVALID_ARG, "V_O view is singular");
     cudaSetDevice(ctx->device);
     vdi_t *v = nullptr;
-    vdi_status st_ = alloc_vdi(ctx, &d, &v);
+    vdi_status st_ = alloc_vdi(ctx, &d, (cudaStream_t)stream, &v);
     if (st_ != VDI_OK) return st_;
 
     GenConsts g{};
@@ -344,7 +348,7 @@ VDI_API vdi_status vdi_generate(vdi_ctx *ctx, const vdi_volume *vol, const vdi_t
     g.fmt = d.colour_fmt;
     cudaStream_t st = (cudaStream_t)stream;
     dim3 grid(div_up(d.w, 32), div_up(d.h, 8));
-    generate_kernel<<<grid, 256, 0, st>>>(g, reinterpret_cast<float4 *>(v->depth_mem), v->colour_mem);
+    generate_kernel<<<grid, 256, 0, st>>>(g, reinterpret_cast<float4 *>(v->depth_mem), v->colour_mem, v->range_mem);
     cudaError_t e = cudaGetLastError();
     if (e == cudaSuccess) e = launch_grid(v->dv, v->grid_mem, st);
     if (e != cudaSuccess) {

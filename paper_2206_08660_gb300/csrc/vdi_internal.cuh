@@ -7,6 +7,9 @@
 //   colour  FP32: float4 [nsp][nl]   (r/a, g/a, b/a, kappa)
 //           FP16: uint4  [nsp/2][nl] (two half4 (r/a, g/a, b/a, kappa) records)
 //   grid    uint32 [nz][gh][gw]  supersegment counts per cell (Section 4.3)
+//   range   float2 [nl]          (front of the first, back of the last supersegment)
+//                                of each list, (+inf, -inf) when empty: a list the
+//                                ray crosses entirely before or after it needs no search
 // nl = w*h lists, nsp = N_S rounded up to even; unused slots hold f = b = +inf
 // and colour 0.  kappa = -log2(1 - alpha): Eq. 2's 1 - (1 - alpha)^l then is
 // 1 - exp2(-kappa l), one exp2 per supersegment piece, and FP16 storage of
@@ -31,6 +34,7 @@ struct DevVdi {
     const float4 *depth;
     const void *colour;
     const uint32_t *grid;
+    const float2 *range;
     int T, gw, gh, nz;
     float edges[kMaxNz + 1];  // slab edges in V_O NDC z, edges[0] = -1, edges[nz] = 1
 };
@@ -70,6 +74,14 @@ template <bool TOUCH>
 __device__ __forceinline__ void mark_depth(const DevVdi &v, uint32_t *bm, int j, int li, int which /*0 f, 1 b*/) {
     if (TOUCH) mark_word<TOUCH>(bm, ((size_t)(j >> 1) * v.nl + li) * 4 + 2 * (j & 1) + which);
 }
+// words of the touch bitmap: depth, then colour, then grid, then list ranges
+__device__ __forceinline__ size_t grid_word_base(const DevVdi &v) {
+    return (size_t)(v.nsp >> 1) * v.nl * 4 * ((v.fmt == 0) ? 3 : 2);
+}
+__device__ __forceinline__ size_t range_word_base(const DevVdi &v) {
+    return grid_word_base(v) + (((size_t)v.nz * v.gh * v.gw + 3) & ~(size_t)3);
+}
+
 template <bool TOUCH>
 __device__ __forceinline__ void mark_colour(const DevVdi &v, uint32_t *bm, int j, int li) {
     if (TOUCH) {

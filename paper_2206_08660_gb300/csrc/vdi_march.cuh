@@ -120,11 +120,19 @@ __device__ __forceinline__ bool process_list(const DevVdi &v, const Seg &g, int 
                                              int &p, Accum &acc, uint32_t &n_lists, uint32_t &n_segs,
                                              uint32_t *bm) {
     const float d_in = fmaf(s_in, g.dz, g.z0), d_out = fmaf(s_out, g.dz, g.z0);
+    ++n_lists;
+    {  // the ray crosses this list entirely before its first or after its last supersegment
+        const float2 rg = __ldg(v.range + li);
+        if (TOUCH) {
+            mark_word<TOUCH>(bm, range_word_base(v) + 2 * (size_t)li);
+            mark_word<TOUCH>(bm, range_word_base(v) + 2 * (size_t)li + 1);
+        }
+        if (fmaxf(d_in, d_out) < rg.x || fminf(d_in, d_out) > rg.y) return false;
+    }
     PairCache pc;
     pc.k = -1;
     ColourCache<FMT> cc;
     cc.k = -1;
-    ++n_lists;
     int last = -1, first;
     if (g.dz >= 0.f) {
         first = first_inc<MODE, TOUCH>(v, li, d_in, p, pc, bm);
@@ -259,76 +267,81 @@ __device__ __forceinline__ void march_exact_ess(const DevVdi &v, Ray &r, Accum &
     while (cz + 1 < v.nz && g.z0 >= v.edges[cz + 1]) ++cz;
     int ez = inc ? cz + 1 : cz;
     float scz = (g.dz != 0.f) ? (v.edges[ez] - g.z0) * g.idz : INFINITY;
+    float sc_in = 0.f, sc_out = 0.f;
     // list walk, (re)started lazily inside occupied cells
     int ix = 0, iy = 0, bx = 0, by = 0;
     float sx = 0.f, sy = 0.f, s_l_in = 0.f;
-    bool lvalid = false;
+    bool lvalid = false, in_cell = false, fresh = true;
     int p = -1;
-    float sc_in = 0.f;
-    const int maxc = v.gw + v.gh + v.nz + 3;
-    for (int it = 0; it < maxc; ++it) {
-        const float sc_out = fminf(fminf(fminf(scx, scy), scz), 1.f);
-        if (sc_out > sc_in) {
-            // grid words follow the depth and colour words in the touch bitmap
-            mark_word<TOUCH>(bm, (size_t)(v.nsp >> 1) * v.nl * 4 * ((v.fmt == 0) ? 3 : 2) +
-                                     ((size_t)cz * v.gh + cy) * v.gw + cx);
-            const uint32_t cnt = __ldg(v.grid + ((size_t)cz * v.gh + cy) * v.gw + cx);
-            if (cnt) {
-                if (!lvalid) {
-                    const float gx = fmaf(sc_in, dgx, gx0), gy = fmaf(sc_in, dgy, gy0);
-                    ix = min(max((int)floorf(gx), cx * T), min(cx * T + T, v.w) - 1);
-                    iy = min(max((int)floorf(gy), cy * T), min(cy * T + T, v.h) - 1);
-                    bx = ix + (dgx > 0.f ? 1 : 0);
-                    by = iy + (dgy > 0.f ? 1 : 0);
-                    sx = (dgx != 0.f) ? ((float)bx - gx0) * idgx : INFINITY;
-                    sy = (dgy != 0.f) ? ((float)by - gy0) * idgy : INFINITY;
-                    s_l_in = sc_in;
-                    lvalid = true;
-                }
-                for (int jt = 0; jt < 2 * T + 2; ++jt) {
-                    const float s_l_out = fminf(sx, sy);
-                    const float a = fmaxf(s_l_in, sc_in), b = fminf(s_l_out, sc_out);
-                    if (b > a) {
-                        if (process_list<FMT, MODE, ERT, TOUCH>(v, g, iy * v.w + ix, a, b, p, acc, n_lists, n_segs,
-                                                                bm))
-                            return;
-                    }
-                    if (s_l_out >= sc_out) break;
-                    if (sx <= sy) {
-                        ix += stx;
-                        if ((unsigned)ix >= (unsigned)v.w) return;
-                        bx += stx;
-                        sx = ((float)bx - gx0) * idgx;
-                    } else {
-                        iy += sty;
-                        if ((unsigned)iy >= (unsigned)v.h) return;
-                        by += sty;
-                        sy = ((float)by - gy0) * idgy;
-                    }
-                    s_l_in = s_l_out;
-                }
-            } else {
-                lvalid = false;
+    // One flat loop: every iteration is either one list step inside an occupied
+    // cell or one cell step, so the lanes of a warp stay in step.
+    const int maxit = 2 * (v.w + v.h) + v.gw + v.gh + v.nz + 8;
+    for (int it = 0; it < maxit; ++it) {
+        if (in_cell) {
+            const float s_l_out = fminf(sx, sy);
+            const float a = fmaxf(s_l_in, sc_in), b = fminf(s_l_out, sc_out);
+            if (b > a &&
+                process_list<FMT, MODE, ERT, TOUCH>(v, g, iy * v.w + ix, a, b, p, acc, n_lists, n_segs, bm))
+                return;
+            if (s_l_out >= sc_out) {  // the list continues beyond this cell
+                in_cell = false;
+                continue;
             }
+            if (sx <= sy) {
+                ix += stx;
+                if ((unsigned)ix >= (unsigned)v.w) return;
+                bx += stx;
+                sx = ((float)bx - gx0) * idgx;
+            } else {
+                iy += sty;
+                if ((unsigned)iy >= (unsigned)v.h) return;
+                by += sty;
+                sy = ((float)by - gy0) * idgy;
+            }
+            s_l_in = s_l_out;
+            continue;
         }
-        if (sc_out >= 1.f) break;
-        if (scx <= scy && scx <= scz) {
-            cx += stx;
-            if ((unsigned)cx >= (unsigned)v.gw) break;
-            bcx += stx * T;
-            scx = ((float)bcx - gx0) * idgx;
-        } else if (scy <= scz) {
-            cy += sty;
-            if ((unsigned)cy >= (unsigned)v.gh) break;
-            bcy += sty * T;
-            scy = ((float)bcy - gy0) * idgy;
-        } else {
-            cz += inc ? 1 : -1;
-            if ((unsigned)cz >= (unsigned)v.nz) break;
-            ez += inc ? 1 : -1;
-            scz = (v.edges[ez] - g.z0) * g.idz;
+        if (!fresh) {  // advance to the next cell
+            if (sc_out >= 1.f) return;
+            if (scx <= scy && scx <= scz) {
+                cx += stx;
+                if ((unsigned)cx >= (unsigned)v.gw) return;
+                bcx += stx * T;
+                scx = ((float)bcx - gx0) * idgx;
+            } else if (scy <= scz) {
+                cy += sty;
+                if ((unsigned)cy >= (unsigned)v.gh) return;
+                bcy += sty * T;
+                scy = ((float)bcy - gy0) * idgy;
+            } else {
+                cz += inc ? 1 : -1;
+                if ((unsigned)cz >= (unsigned)v.nz) return;
+                ez += inc ? 1 : -1;
+                scz = (v.edges[ez] - g.z0) * g.idz;
+            }
+            sc_in = fmaxf(sc_in, sc_out);
         }
-        sc_in = fmaxf(sc_in, sc_out);
+        fresh = false;
+        sc_out = fminf(fminf(fminf(scx, scy), scz), 1.f);
+        if (!(sc_out > sc_in)) continue;
+        const size_t cell = ((size_t)cz * v.gh + cy) * v.gw + cx;
+        mark_word<TOUCH>(bm, grid_word_base(v) + cell);
+        if (__ldg(v.grid + cell) == 0u) {
+            lvalid = false;
+            continue;
+        }
+        if (!lvalid) {
+            const float gx = fmaf(sc_in, dgx, gx0), gy = fmaf(sc_in, dgy, gy0);
+            ix = min(max((int)floorf(gx), cx * T), min(cx * T + T, v.w) - 1);
+            iy = min(max((int)floorf(gy), cy * T), min(cy * T + T, v.h) - 1);
+            bx = ix + (dgx > 0.f ? 1 : 0);
+            by = iy + (dgy > 0.f ? 1 : 0);
+            sx = (dgx != 0.f) ? ((float)bx - gx0) * idgx : INFINITY;
+            sy = (dgy != 0.f) ? ((float)by - gy0) * idgy : INFINITY;
+            s_l_in = sc_in;
+            lvalid = true;
+        }
+        in_cell = true;
     }
 }
 
@@ -397,6 +410,8 @@ __device__ __forceinline__ void march_preview(const DevVdi &v, const ViewConsts 
                         cc.k = -1;
                         plist = li;
                     }
+                    const float2 rg = __ldg(v.range + li);
+                    if (nz < rg.x || nz > rg.y) continue;  // outside every supersegment of the list
                     const int j = first_inc<MODE>(v, li, nz, p, pc);
                     p = min(j, v.nsp - 1);
                     if (j < v.nsp) {

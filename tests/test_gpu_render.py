@@ -207,8 +207,9 @@ def test_invalid_inputs_are_reported(V, ctx):
 @pytest.mark.parametrize("fmt", [0, 1])
 def test_empty_space_skipping_changes_nothing(V, ctx, fmt):
     """Section 4.3: cells whose count is 0 hold no supersegment, so skipping them
-    leaves the image unchanged (up to the rounding of splitting a supersegment
-    piece at cell boundaries)."""
+    leaves the image unchanged, up to where early termination lands: pieces
+    split at cell boundaries can stop the ray one piece earlier, and whatever
+    follows a transmittance of 2^-12 weighs at most 2^-12."""
     for seed, fill in ((4, 0.3), (5, 0.9)):
         case = random_case(96, 64, 6, seed=seed, fill=fill)
         vdi = V.vdi_create(ctx, case.gpu_desc(V, fmt, T=8, nz=16), case.vdi.rgba, case.vdi.depth, case.vdi.counts)
@@ -217,6 +218,6 @@ def test_empty_space_skipping_changes_nothing(V, ctx, fmt):
                 cn = S.orbit_camera(case.bmin, case.bmax, 1.25, az_deg=az, el_deg=el, zoom=zoom, ortho=ortho)
                 a = gpu_render(V, vdi, cn, 80, 64)
                 b = gpu_render(V, vdi, cn, 80, 64, no_ess=True)
-                assert np.abs(a - b).max() < 2e-5, (seed, az)
+                assert np.abs(a - b).max() <= 2.0 ** -12, (seed, az)
         finally:
             V.vdi_destroy(vdi)
