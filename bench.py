@@ -210,6 +210,143 @@ class OracleLeg:
                 f"to full frames; oracle VDI from the oracle's own FP32 generation")
 
 
+SERVING = dict(n_vdis=8, w=1920, h=1080, ns=24, tau=0.01, vol_n=512, rate=240.0, seconds=8.0, replace_every=2.0,
+               budget=24 << 30, max_batch=32, max_inflight=3,
+               res=[(640, 360), (1280, 720), (1280, 720), (1920, 1080)], max_dev=45.0, seed=7)
+
+
+def serving_leg(V, torch, ctx, dev, cfg=SERVING):
+    """Continuous-batching server under Poisson arrivals, p50/p99 latency and throughput.
+
+    8 resident 1920x1080 N_S=24 FP16 VDIs (from a seeded 512^3 uint8 noise volume
+    seen from 8 directions); arrivals at `rate` requests/s; resolution mix
+    360p:720p:1080p = 1:2:1; deviation U[0, 45] deg; D_I, D_R in {1, 2}; every
+    2 s one slot gets a freshly generated VDI from a side stream.  Also measures
+    saturated throughput of the same request mix through the server (batched,
+    FP16 colour) and through one vdi_render per request on FP32-colour VDIs."""
+    import threading as th
+
+    rng = np.random.default_rng(cfg["seed"])
+    vol = S.value_noise_volume(cfg["vol_n"], seed=cfg["seed"], dtype=np.uint8)
+    bmin, bmax = S.bbox_for_dims(vol.shape)
+    u = 1.0 / cfg["vol_n"]
+    vol_d = torch.from_numpy(vol).to(dev)
+    kn = S.tf_knots("sparse")
+    az0 = [45.0 * k for k in range(cfg["n_vdis"])]
+    cams_o = [S.orbit_camera(bmin, bmax, cfg["w"] / cfg["h"], az_deg=a, el_deg=20.0) for a in az0]
+
+    def gen(k, fmt, az=None, stream=None):
+        c = cams_o[k] if az is None else S.orbit_camera(bmin, bmax, cfg["w"] / cfg["h"], az_deg=az, el_deg=20.0)
+        return V.vdi_generate(ctx, vol_d, bmin, bmax, kn, V.camera(c.view, c.proj), cfg["w"], cfg["h"], cfg["ns"],
+                              cfg["tau"], u, u, fmt, stream=stream), c
+
+    def make_requests(n):
+        reqs = []
+        for _ in range(n):
+            slot = int(rng.integers(0, cfg["n_vdis"]))
+            W, H = cfg["res"][int(rng.integers(0, len(cfg["res"])))]
+            dev_deg = float(rng.uniform(0.0, cfg["max_dev"])) * (1 if rng.random() < 0.5 else -1)
+            cam = S.orbit_camera(bmin, bmax, W / H, az_deg=az0[slot] + dev_deg, el_deg=20.0)
+            d_i, d_r = int(rng.integers(1, 3)), int(rng.integers(1, 3))
+            reqs.append((slot, V.camera(cam.view, cam.proj), W, H, d_i, d_r))
+        return reqs
+
+    srv = V.vdi_server_create(ctx, cfg["budget"], cfg["max_batch"], cfg["max_inflight"], cfg["n_vdis"])
+    side = torch.cuda.Stream()
+    try:
+        for k in range(cfg["n_vdis"]):
+            V.vdi_server_set_vdi(srv, k, gen(k, V.VDI_F16)[0])
+        torch.cuda.synchronize()
+        # warm-up: every resolution / preview combination once
+        for (slot, cam, W, H, d_i, d_r) in make_requests(32):
+            t = V.vdi_server_submit(srv, V.view_request(slot, cam, W, H, d_i, d_r))
+            V.vdi_server_wait(srv, t, 30.0)
+            V.vdi_server_release(srv, t)
+
+        # ---- open loop: Poisson arrivals
+        n = int(cfg["rate"] * cfg["seconds"])
+        arrivals = np.cumsum(rng.exponential(1.0 / cfg["rate"], size=n))
+        reqs = make_requests(n)
+        tickets = [None] * n
+        lat, fails = [], 0
+        t_start = time.monotonic()
+
+        def submitter():
+            for i in range(n):
+                d = t_start + arrivals[i] - time.monotonic()
+                if d > 0:
+                    time.sleep(d)
+                slot, cam, W, H, d_i, d_r = reqs[i]
+                tickets[i] = V.vdi_server_submit(srv, V.view_request(slot, cam, W, H, d_i, d_r))
+
+        def replacer():
+            k = 0
+            while time.monotonic() - t_start < arrivals[-1]:
+                time.sleep(cfg["replace_every"])
+                slot = k % cfg["n_vdis"]
+                with torch.cuda.stream(side):
+                    vdi, _ = gen(slot, V.VDI_F16, az=az0[slot] + 5.0 * (k + 1), stream=side)
+                V.vdi_server_set_vdi(srv, slot, vdi, side)
+                k += 1
+
+        ts, tr = th.Thread(target=submitter), th.Thread(target=replacer)
+        ts.start()
+        tr.start()
+        for i in range(n):
+            while tickets[i] is None:
+                time.sleep(0.0002)
+            info = V.vdi_server_wait(srv, tickets[i], 30.0)
+            if info.status != 0:
+                fails += 1
+            else:
+                lat.append((info.t_done - info.t_submit) * 1e3)
+            V.vdi_server_release(srv, tickets[i])
+        ts.join()
+        tr.join()
+        wall = time.monotonic() - t_start
+        st = V.vdi_server_stats(srv)
+        lat = np.array(lat)
+        open_loop = {"offered_rps": cfg["rate"], "requests": n, "failed": fails,
+                     "p50_ms": float(np.percentile(lat, 50)), "p99_ms": float(np.percentile(lat, 99)),
+                     "throughput_rps": len(lat) / wall, "mean_batch": st.batched_requests / max(st.batches, 1),
+                     "vdi_replacements": int(st.vdi_installs) - cfg["n_vdis"]}
+
+        # ---- saturated throughput, same request mix: batched server (FP16) ...
+        sat = make_requests(512)
+        torch.cuda.synchronize()
+        t0 = time.monotonic()
+        ids = [V.vdi_server_submit(srv, V.view_request(*r)) for r in sat]
+        for t in ids:
+            V.vdi_server_wait(srv, t, 60.0)
+            V.vdi_server_release(srv, t)
+        batched_rps = len(sat) / (time.monotonic() - t0)
+    finally:
+        V.vdi_server_destroy(srv)
+    # ... against one vdi_render per request on FP32-colour VDIs
+    vdis32 = [gen(k, V.VDI_F32)[0] for k in range(cfg["n_vdis"])]
+    outs = {}
+    for (slot, cam, W, H, d_i, d_r) in sat:
+        outs.setdefault((W, H), torch.empty((H, W, 4), dtype=torch.float32, device=dev))
+    for (slot, cam, W, H, d_i, d_r) in sat[:16]:
+        V.vdi_render(vdis32[slot], cam, W, H, d_i, d_r, outs[(W, H)], V.VDI_F32)
+    torch.cuda.synchronize()
+    t0 = time.monotonic()
+    for (slot, cam, W, H, d_i, d_r) in sat:
+        V.vdi_render(vdis32[slot], cam, W, H, d_i, d_r, outs[(W, H)], V.VDI_F32)
+    torch.cuda.synchronize()
+    single_rps = len(sat) / (time.monotonic() - t0)
+    for v in vdis32:
+        V.vdi_destroy(v)
+    del vol_d
+    torch.cuda.empty_cache()
+    return {"workload": "8 resident 1920x1080 N_S=24 FP16 VDIs (512^3 u8 noise), Poisson 240 req/s, "
+                        "360p:720p:1080p = 1:2:1, deviation U[0,45] deg, D_I,D_R in {1,2}, one VDI replaced "
+                        "every 2 s from a side stream, 24 GB budget",
+            "open_loop": open_loop,
+            "saturated": {"batched_fp16_server_rps": batched_rps, "one_view_per_launch_fp32_rps": single_rps,
+                          "requests": len(sat)}}
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -218,6 +355,7 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="large", choices=list(WORKLOADS))
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-serving", action="store_true")
     ap.add_argument("--cpu-budget", type=float, default=15.0, help="seconds of oracle work for cpu_baseline")
     args = ap.parse_args()
     wl = WORKLOADS[args.workload]
@@ -337,6 +475,28 @@ def main():
     peak, peak_src = peaks()
     traffic = recorded_traffic(args.workload)
 
+    # ---- ablations on the exact frames (not part of the timed step): empty-space
+    # skipping off, and the baseline first-supersegment searches of Fig. 4
+    def time_variant(**kw):
+        ms = []
+        for i in exact:
+            evs_v = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(8)]
+            for rep in range(8):
+                flush.fill_(float(rep))
+                evs_v[rep][0].record(stream)
+                V.vdi_render_ex(vdi, cams[i], W, H, 1, 1, outs[i], V.VDI_F16, stream=stream, **kw)
+                evs_v[rep][1].record(stream)
+            torch.cuda.synchronize()
+            ms.append(float(np.mean([a.elapsed_time(b) for a, b in evs_v[3:]])))
+        return [round(m, 4) for m in ms]
+
+    ablation = {"exact_frames_deg": [wl["frames"][i][0] for i in exact],
+                "default_ms": time_variant(),
+                "ess_ms": time_variant(ess=True),
+                "binary_search_ms": time_variant(search=V.VDI_SEARCH_BINARY),
+                "linear_search_ms": time_variant(search=V.VDI_SEARCH_LINEAR),
+                "note": "ms per exact frame, CUDA events, L2 flushed before each repetition"}
+
     # ---- end to end through the public API: render + read back to pinned host memory
     host = [torch.empty((H, W, 4), dtype=torch.float16, pin_memory=True) for _ in wl["frames"]]
     cam_bytes = 2 * 16 * 8
@@ -365,9 +525,14 @@ def main():
                      "frac": achieved / peak, "traffic": traffic, "peak_source": peak_src,
                      "kernel": "render_kernel (exact path)",
                      "algorithmic_bytes_per_launch": [int(b) for b in touched]},
-        "clocks": clocks, "e2e": e2e, "gpu_launches": launches_per_step * args.steps,
+        "clocks": clocks, "e2e": e2e, "gpu_launches": launches_per_step * args.steps, "ablation": ablation,
         "vdi_generate_ms": gen_s * 1e3, "vdi_bytes": int(layout.depth_bytes + layout.colour_bytes),
     }
+    if not args.no_serving:
+        srv = serving_leg(V, torch, ctx, dev)
+        result["serving"] = srv
+        result["serving_p50_ms"] = srv["open_loop"]["p50_ms"]
+        result["serving_p99_ms"] = srv["open_loop"]["p99_ms"]
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         try:
             leg = OracleLeg(wl, vol, bmin, bmax, u, cam_o, views)

@@ -103,9 +103,10 @@ typedef struct {
     uint32_t *ray_lists; /* nullable device [H'][W']: lists traversed with positive length per ray */
     uint32_t *ray_segs;  /* nullable device [H'][W']: supersegment pieces of positive length per ray */
     int warp_shape;      /* -1: default/autotuned; 0: 32x1, 1: 16x2, 2: 8x4 pixels per warp */
-    int no_ess;          /* 1: walk every list the ray crosses (no empty-space skipping, Section 4.3).
-                            The image is the same either way; per-ray counters always come from the
-                            walk over every list. */
+    int ess;             /* 1: empty-space skipping over the count grid (Section 4.3): occupied cells
+                            only.  Off by default (measured slower on the benchmark workloads); the
+                            image is the same up to where early termination lands; per-ray
+                            counters always come from the walk over every list. */
 } vdi_render_opts;
 
 /* ---- context ---------------------------------------------------------- */

@@ -223,12 +223,26 @@ vdi_status make_view_consts(const vdi_t *v, const vdi_camera *cam, int W, int H,
     const double *M = v->M;
     double e0[4] = {O0[0], O0[1], O0[2], 1.0}, ex[4] = {Ox[0], Ox[1], Ox[2], 0.0}, ey[4] = {Oy[0], Oy[1], Oy[2], 0.0};
     double f0[4] = {D0[0], D0[1], D0[2], 0.0}, fx[4] = {Dx[0], Dx[1], Dx[2], 0.0}, fy[4] = {Dy[0], Dy[1], Dy[2], 0.0};
-    mat4_apply(M, e0, c->A0);
-    mat4_apply(M, ex, c->Ax);
-    mat4_apply(M, ey, c->Ay);
-    mat4_apply(M, f0, c->B0);
-    mat4_apply(M, fx, c->Bx);
-    mat4_apply(M, fy, c->By);
+    double A0[4], Ax[4], Ay[4], B0[4], Bx[4], By[4];
+    mat4_apply(M, e0, A0);
+    mat4_apply(M, ex, Ax);
+    mat4_apply(M, ey, Ay);
+    mat4_apply(M, f0, B0);
+    mat4_apply(M, fx, Bx);
+    mat4_apply(M, fy, By);
+    // fold the pixel-centre map x = (px + 1/2) 2/W - 1, y = 1 - (py + 1/2) 2/H into
+    // affine forms of the integer pixel indices: a = A0' + px Ax' + py Ay'
+    const double sx = 2.0 / W, sy = 2.0 / H;
+    for (int k = 0; k < 4; ++k) {
+        c->A0[k] = A0[k] + (0.5 * sx - 1.0) * Ax[k] + (1.0 - 0.5 * sy) * Ay[k];
+        c->Ax[k] = sx * Ax[k];
+        c->Ay[k] = -sy * Ay[k];
+        c->B0[k] = B0[k] + (0.5 * sx - 1.0) * Bx[k] + (1.0 - 0.5 * sy) * By[k];
+        c->Bx[k] = sx * Bx[k];
+        c->By[k] = -sy * By[k];
+        c->A0f[k] = (float)c->A0[k];
+        c->B0f[k] = (float)c->B0[k];
+    }
     c->a_affine = a_aff;
     c->b_affine = b_aff;
     for (int k = 0; k < 3; ++k) {
@@ -532,11 +546,10 @@ VDI_API vdi_status vdi_render_ex(vdi_t *v, const vdi_camera *view, int W, int H,
     const int ws = o.warp_shape >= 0 ? o.warp_shape : default_warp_shape(v, Wr, Hr);
     float4 *lo = nullptr;
     if (d_i == 1) {
-        CK(launch_render(c, v->dv, out_rgba, out_fmt, o.ray_lists, o.ray_segs, o.search, ws, !o.no_ert, !o.no_ess,
-                         st));
+        CK(launch_render(c, v->dv, out_rgba, out_fmt, o.ray_lists, o.ray_segs, o.search, ws, !o.no_ert, o.ess != 0, st));
     } else {
         CK(cudaMallocAsync((void **)&lo, (size_t)Wr * Hr * sizeof(float4), st));
-        CK(launch_render(c, v->dv, lo, VDI_F32, o.ray_lists, o.ray_segs, o.search, ws, !o.no_ert, !o.no_ess, st));
+        CK(launch_render(c, v->dv, lo, VDI_F32, o.ray_lists, o.ray_segs, o.search, ws, !o.no_ert, o.ess != 0, st));
         CK(launch_upsample(lo, Wr, Hr, out_rgba, out_fmt, W, H, st));
     }
 done:

@@ -46,8 +46,11 @@ struct DevVdi {
 // b = P_O V_O (D, 0), both affine in (x, y); a is constant for a perspective
 // V_N (O = eye), b is constant for an orthographic one.
 struct ViewConsts {
+    // a(px, py) = A0 + px Ax + py Ay for integer pixel indices (pixel centres
+    // and the NDC scale folded in on the host), likewise b
     double A0[4], Ax[4], Ay[4];
     double B0[4], Bx[4], By[4];
+    float A0f[4], B0f[4];  // the same constants rounded to FP32, for the non-affine case
     int a_affine, b_affine;
     float O0[3], Ox[3], Oy[3];
     float D0[3], Dx[3], Dy[3];

@@ -37,15 +37,16 @@ __device__ __forceinline__ void clip_lin(float c0, float c1, float &t0, float &t
 // Ray setup (Section 4.1): FP64 only for the map of the pixel's ray into V_O
 // clip space (a, b); everything after it is FP32.
 __device__ __forceinline__ bool setup_ray(const ViewConsts &c, int px, int py, Ray &r) {
-    const double x = fma((double)px + 0.5, c.sx, -1.0);
-    const double y = fma(-((double)py + 0.5), c.sy, 1.0);
+    const double dpx = (double)px, dpy = (double)py;
     float a[4], b[4];
 #pragma unroll
     for (int k = 0; k < 4; ++k) {
-        a[k] = c.a_affine ? (float)fma(y, c.Ay[k], fma(x, c.Ax[k], c.A0[k])) : (float)c.A0[k];
-        b[k] = c.b_affine ? (float)fma(y, c.By[k], fma(x, c.Bx[k], c.B0[k])) : (float)c.B0[k];
+        a[k] = c.a_affine ? (float)fma(dpy, c.Ay[k], fma(dpx, c.Ax[k], c.A0[k])) : c.A0f[k];
+        b[k] = c.b_affine ? (float)fma(dpy, c.By[k], fma(dpx, c.Bx[k], c.B0[k])) : c.B0f[k];
     }
-    const float xf = (float)x, yf = (float)y;
+    // pixel centre in V_N NDC (FP32 is enough for the world-space box clip)
+    const float x = fmaf((float)px + 0.5f, (float)c.sx, -1.f), y = fmaf(-((float)py + 0.5f), (float)c.sy, 1.f);
+    const float xf = x, yf = y;
     float t0 = c.t_lo, t1 = c.t_hi;
 #pragma unroll
     for (int k = 0; k < 3; ++k) {

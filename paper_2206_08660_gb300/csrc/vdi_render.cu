@@ -55,7 +55,7 @@ __global__ void __launch_bounds__(256) touch_kernel(const ViewConsts c, const De
     Accum acc = {0.f, 0.f, 0.f, 1.f};
     uint32_t nl = 0, nsg = 0;
     Ray r;
-    if (setup_ray(c, px, py, r)) march_exact_ess<FMT, kSearchAlg2, true, true>(v, r, acc, nl, nsg, bm);
+    if (setup_ray(c, px, py, r)) march_exact<FMT, kSearchAlg2, true, true>(v, r, acc, nl, nsg, bm);
 }
 
 cudaError_t launch_touch(const ViewConsts &c, const DevVdi &v, uint32_t *bm, cudaStream_t st) {

@@ -216,8 +216,8 @@ def test_empty_space_skipping_changes_nothing(V, ctx, fmt):
         try:
             for (az, el, zoom, ortho) in VIEWS:
                 cn = S.orbit_camera(case.bmin, case.bmax, 1.25, az_deg=az, el_deg=el, zoom=zoom, ortho=ortho)
-                a = gpu_render(V, vdi, cn, 80, 64)
-                b = gpu_render(V, vdi, cn, 80, 64, no_ess=True)
+                a = gpu_render(V, vdi, cn, 80, 64, ess=True)
+                b = gpu_render(V, vdi, cn, 80, 64)
                 assert np.abs(a - b).max() <= 2.0 ** -12, (seed, az)
         finally:
             V.vdi_destroy(vdi)
