@@ -63,6 +63,7 @@ struct UpParams {
 template <int WX>
 __global__ void __launch_bounds__(256) batch_render_kernel(const BatchParams P) {
     __shared__ int s_tile, s_req;
+    __shared__ TileRays tr;
     for (;;) {
         if (threadIdx.x == 0) {
             const int t = (int)atomicAdd(P.counter, 1u);
@@ -83,20 +84,20 @@ __global__ void __launch_bounds__(256) batch_render_kernel(const BatchParams P) 
         }
         __syncthreads();
         const int tile = s_tile, r = s_req;
-        __syncthreads();
-        if (tile >= P.total_tiles) return;
+        if (tile >= P.total_tiles) return;  // uniform: every thread read the same s_tile
         const BatchReq &q = P.reqs[r];
         const DevVdi &v = P.vdis[q.vdi];
         const int local = tile - q.tile_base;
-        int px, py;
-        tile_offset<WX>(px, py);
-        px += (local % q.tiles_x) * 32;
-        py += (local / q.tiles_x) * 8;
+        const int tx0 = (local % q.tiles_x) * 32, ty0 = (local / q.tiles_x) * 8;
+        tile_rays(q.c, tx0, ty0, tr);  // synchronises: s_tile / s_req are read before the next write
+        int lx, ly;
+        tile_offset<WX>(lx, ly);
+        const int px = tx0 + lx, py = ty0 + ly;
         if (px < q.c.W && py < q.c.H) {
             Accum acc = {0.f, 0.f, 0.f, 1.f};
             uint32_t nl = 0, nsg = 0;
             Ray ray;
-            if (setup_ray(q.c, px, py, ray)) {
+            if (setup_ray(q.c, tr, px, py, lx, ly, ray)) {
                 if (q.c.d_r > 1) {
                     if (v.fmt == 0)
                         march_preview<0, kSearchAlg2, true>(v, q.c, ray, acc);
@@ -111,6 +112,7 @@ __global__ void __launch_bounds__(256) batch_render_kernel(const BatchParams P) 
             }
             store_px(q.out, q.out_fmt, (size_t)py * q.c.W + px, acc);
         }
+        __syncthreads();  // the tile's shared ray terms are read until here
     }
 }
 

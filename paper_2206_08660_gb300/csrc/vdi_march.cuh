@@ -34,15 +34,54 @@ __device__ __forceinline__ void clip_lin(float c0, float c1, float &t0, float &t
         t1 = -INFINITY;
 }
 
+// FP64 affine terms of the rays of one 32 x 8 pixel tile, in shared memory:
+// b(px, py) = (B0 + py By) + px Bx = R[py - ty0] + C[px - tx0] (likewise a), so
+// each ray adds one row and one column term in FP64 instead of evaluating the
+// whole affine form.  [component][row / column] keeps the lane reads
+// conflict-free.
+struct TileRays {
+    double bR[4][8], bC[4][32];
+    double aR[4][8], aC[4][32];
+};
+
+// All threads of the block must call this (it synchronises).
+__device__ __forceinline__ void tile_rays(const ViewConsts &c, int tx0, int ty0, TileRays &tr) {
+    const int t = threadIdx.x;
+    if (c.b_affine) {
+        if (t < 32) {
+            const double dpx = (double)(tx0 + t);
+#pragma unroll
+            for (int k = 0; k < 4; ++k) tr.bC[k][t] = dpx * c.Bx[k];
+        } else if (t < 40) {
+            const double dpy = (double)(ty0 + t - 32);
+#pragma unroll
+            for (int k = 0; k < 4; ++k) tr.bR[k][t - 32] = fma(dpy, c.By[k], c.B0[k]);
+        }
+    }
+    if (c.a_affine) {
+        if (t >= 64 && t < 96) {
+            const double dpx = (double)(tx0 + t - 64);
+#pragma unroll
+            for (int k = 0; k < 4; ++k) tr.aC[k][t - 64] = dpx * c.Ax[k];
+        } else if (t >= 96 && t < 104) {
+            const double dpy = (double)(ty0 + t - 96);
+#pragma unroll
+            for (int k = 0; k < 4; ++k) tr.aR[k][t - 96] = fma(dpy, c.Ay[k], c.A0[k]);
+        }
+    }
+    __syncthreads();
+}
+
 // Ray setup (Section 4.1): FP64 only for the map of the pixel's ray into V_O
-// clip space (a, b); everything after it is FP32.
-__device__ __forceinline__ bool setup_ray(const ViewConsts &c, int px, int py, Ray &r) {
-    const double dpx = (double)px, dpy = (double)py;
+// clip space (a, b); everything after it is FP32.  (lx, ly) is the pixel's
+// place in its tile.
+__device__ __forceinline__ bool setup_ray(const ViewConsts &c, const TileRays &tr, int px, int py, int lx, int ly,
+                                          Ray &r) {
     float a[4], b[4];
 #pragma unroll
     for (int k = 0; k < 4; ++k) {
-        a[k] = c.a_affine ? (float)fma(dpy, c.Ay[k], fma(dpx, c.Ax[k], c.A0[k])) : c.A0f[k];
-        b[k] = c.b_affine ? (float)fma(dpy, c.By[k], fma(dpx, c.Bx[k], c.B0[k])) : c.B0f[k];
+        a[k] = c.a_affine ? (float)(tr.aR[k][ly] + tr.aC[k][lx]) : c.A0f[k];
+        b[k] = c.b_affine ? (float)(tr.bR[k][ly] + tr.bC[k][lx]) : c.B0f[k];
     }
     // pixel centre in V_N NDC (FP32 is enough for the world-space box clip)
     const float x = fmaf((float)px + 0.5f, (float)c.sx, -1.f), y = fmaf(-((float)py + 0.5f), (float)c.sy, 1.f);
