@@ -90,7 +90,8 @@ typedef struct {
     size_t depth_bytes;  /* front/back FP32 depths on the device */
     size_t colour_bytes; /* colour + opacity on the device */
     size_t grid_bytes;   /* uint32 supersegment counts */
-    size_t list_bytes;   /* per list: front of its first and back of its last supersegment (float2) */
+    size_t list_bytes;   /* per list, then per block of 4 x 4 lists: front of the first and back of the last
+                            supersegment (float2 each) */
     size_t total_bytes;  /* everything the VDI holds on the device */
     size_t paper_bytes;  /* size in the paper's RGBA32F + 2 x R32F layout: 24 B per slot (Section 5) */
     int grid_w, grid_h, grid_nz;
@@ -107,6 +108,8 @@ typedef struct {
                             only.  Off by default (measured slower on the benchmark workloads); the
                             image is the same up to where early termination lands; per-ray
                             counters always come from the walk over every list. */
+    int no_blocks;       /* 1: do not skip 4 x 4 blocks of lists whose depth range the ray misses
+                            (the image is identical either way) */
 } vdi_render_opts;
 
 /* ---- context ---------------------------------------------------------- */

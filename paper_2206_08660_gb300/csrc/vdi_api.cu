@@ -19,7 +19,7 @@
 namespace vdi {
 
 cudaError_t launch_render(const ViewConsts &c, const DevVdi &v, void *out, int out_fmt, uint32_t *rl,
-                          uint32_t *rs, int search, int warp_shape, bool ert, bool ess, cudaStream_t st);
+                          uint32_t *rs, int search, int warp_shape, bool ert, bool ess, bool blocks, cudaStream_t st);
 cudaError_t launch_touch(const ViewConsts &c, const DevVdi &v, uint32_t *bm, cudaStream_t st);
 cudaError_t launch_upsample(const float4 *lo, int w0, int h0, void *out, int out_fmt, int W, int H,
                             cudaStream_t st);
@@ -134,7 +134,7 @@ vdi_status check_desc(const vdi_desc *d, vdi_layout *L) {
     L->grid_h = div_up(d->h, T);
     L->grid_nz = nz;
     L->grid_bytes = (size_t)L->grid_w * L->grid_h * nz * sizeof(uint32_t);
-    L->list_bytes = nl * 2 * sizeof(float);
+    L->list_bytes = nl * 2 * sizeof(float) + (size_t)div_up(d->w, kB) * div_up(d->h, kB) * 2 * sizeof(float);
     L->total_bytes = L->depth_bytes + L->colour_bytes + L->grid_bytes + L->list_bytes;
     L->paper_bytes = nl * (size_t)d->n_s * 24;
     return VDI_OK;
@@ -398,6 +398,10 @@ vdi_status alloc_vdi(vdi_ctx *ctx, const vdi_desc *desc, cudaStream_t stream, vd
     d.colour = v->colour_mem;
     d.grid = v->grid_mem;
     d.range = v->range_mem;
+    d.bw = div_up(desc->w, kB);
+    d.bh = div_up(desc->h, kB);
+    v->brange_mem = v->range_mem + d.nl;  // the block ranges follow the list ranges
+    d.brange = v->brange_mem;
     *out = v;
     return VDI_OK;
 }
@@ -454,6 +458,7 @@ VDI_API vdi_status vdi_create(vdi_ctx *ctx, const vdi_desc *desc, const float *r
                       reinterpret_cast<float4 *>(v->depth_mem), v->colour_mem, d_err, st));
     CK(launch_grid(v->dv, v->grid_mem, st));
     CK(launch_range(d_depth, d_counts, desc->n_s, (long long)nl, v->range_mem, st));
+    CK(launch_block_range(v->dv, v->brange_mem, st));
     CK(cudaMemcpyAsync(&h_err, d_err, sizeof(unsigned), cudaMemcpyDeviceToHost, st));
     CK(cudaStreamSynchronize(st));
     if (h_err & 1u)
@@ -514,7 +519,7 @@ namespace vdi {
 // length in uint32 of the touch bitmap: depth, colour, grid padded to 16 bytes, list ranges
 size_t touch_words(const vdi_t *v) {
     const size_t grid_words = ((size_t)v->dv.nz * v->dv.gh * v->dv.gw + 3) & ~(size_t)3;
-    const size_t words = (v->layout.depth_bytes + v->layout.colour_bytes) / 4 + grid_words + v->layout.list_bytes / 4;
+    const size_t words = (v->layout.depth_bytes + v->layout.colour_bytes) / 4 + grid_words + v->layout.list_bytes / 4;  // list and block ranges
     return (words + 31) / 32;
 }
 
@@ -533,7 +538,7 @@ VDI_API vdi_status vdi_render_ex(vdi_t *v, const vdi_camera *view, int W, int H,
                                  void *out_rgba, int out_fmt, const vdi_render_opts *opts, void *stream) {
     vdi_status st_ = check_render_args(v, W, H, d_i, d_r, out_rgba, out_fmt);
     if (st_ != VDI_OK) return st_;
-    vdi_render_opts o = {VDI_SEARCH_ALG2, 0, nullptr, nullptr, -1, 0};
+    vdi_render_opts o = {VDI_SEARCH_ALG2, 0, nullptr, nullptr, -1, 0, 0};
     if (opts) o = *opts;
     if (o.search < 0 || o.search > 2) return fail(VDI_ERR_INVALID_ARG, "search=%d", o.search);
     if (o.warp_shape < -1 || o.warp_shape > 2) return fail(VDI_ERR_INVALID_ARG, "warp_shape=%d", o.warp_shape);
@@ -546,10 +551,10 @@ VDI_API vdi_status vdi_render_ex(vdi_t *v, const vdi_camera *view, int W, int H,
     const int ws = o.warp_shape >= 0 ? o.warp_shape : default_warp_shape(v, Wr, Hr);
     float4 *lo = nullptr;
     if (d_i == 1) {
-        CK(launch_render(c, v->dv, out_rgba, out_fmt, o.ray_lists, o.ray_segs, o.search, ws, !o.no_ert, o.ess != 0, st));
+        CK(launch_render(c, v->dv, out_rgba, out_fmt, o.ray_lists, o.ray_segs, o.search, ws, !o.no_ert, o.ess != 0, !o.no_blocks, st));
     } else {
         CK(cudaMallocAsync((void **)&lo, (size_t)Wr * Hr * sizeof(float4), st));
-        CK(launch_render(c, v->dv, lo, VDI_F32, o.ray_lists, o.ray_segs, o.search, ws, !o.no_ert, o.ess != 0, st));
+        CK(launch_render(c, v->dv, lo, VDI_F32, o.ray_lists, o.ray_segs, o.search, ws, !o.no_ert, o.ess != 0, !o.no_blocks, st));
         CK(launch_upsample(lo, Wr, Hr, out_rgba, out_fmt, W, H, st));
     }
 done:

@@ -23,6 +23,7 @@ struct vdi_t {
     void *colour_mem = nullptr;
     uint32_t *grid_mem = nullptr;
     float2 *range_mem = nullptr;
+    float2 *brange_mem = nullptr;
 };
 
 namespace vdi {
@@ -40,6 +41,7 @@ void grid_edges(const double *P, int nz, float *edges);
 size_t touch_words(const vdi_t *v);
 vdi_status check_render_args(const vdi_t *v, int W, int H, int d_i, int d_r, const void *out, int out_fmt);
 void release_batch_cache(vdi_ctx *ctx);
+cudaError_t launch_block_range(const DevVdi &v, float2 *brange, cudaStream_t st);
 
 // warp shape used when the caller does not choose one: 32x1 (lanes along a
 // row of lists) unless the autotuner recorded a better one

@@ -131,6 +131,25 @@ __global__ void range_kernel(const float *__restrict__ depth, const int32_t *__r
                   : make_float2(INFINITY, -INFINITY);
 }
 
+// Per block of kB x kB lists: the smallest first front and the largest last back.
+__global__ void block_range_kernel(const DevVdi v, float2 *__restrict__ brange) {
+    const int bxi = blockIdx.x * blockDim.x + threadIdx.x, byi = blockIdx.y;
+    if (bxi >= v.bw) return;
+    float lo = INFINITY, hi = -INFINITY;
+    for (int y = byi * kB; y < min(byi * kB + kB, v.h); ++y)
+        for (int x = bxi * kB; x < min(bxi * kB + kB, v.w); ++x) {
+            const float2 r = v.range[(size_t)y * v.w + x];
+            lo = fminf(lo, r.x);
+            hi = fmaxf(hi, r.y);
+        }
+    brange[(size_t)byi * v.bw + bxi] = make_float2(lo, hi);
+}
+
+cudaError_t launch_block_range(const DevVdi &v, float2 *brange, cudaStream_t st) {
+    block_range_kernel<<<dim3(div_up(v.bw, 128), v.bh), 128, 0, st>>>(v, brange);
+    return cudaGetLastError();
+}
+
 // Device layout -> array-of-structures (premultiplied rgba, alpha per unit).
 template <int FMT>
 __global__ void download_kernel(const DevVdi v, int ns, float *__restrict__ rgba, float *__restrict__ depth,

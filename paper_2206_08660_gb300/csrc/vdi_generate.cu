@@ -351,6 +351,7 @@ VDI_API vdi_status vdi_generate(vdi_ctx *ctx, const vdi_volume *vol, const vdi_t
     generate_kernel<<<grid, 256, 0, st>>>(g, reinterpret_cast<float4 *>(v->depth_mem), v->colour_mem, v->range_mem);
     cudaError_t e = cudaGetLastError();
     if (e == cudaSuccess) e = launch_grid(v->dv, v->grid_mem, st);
+    if (e == cudaSuccess) e = launch_block_range(v->dv, v->brange_mem, st);
     if (e != cudaSuccess) {
         cudaStreamSynchronize(st);
         free_vdi(v);

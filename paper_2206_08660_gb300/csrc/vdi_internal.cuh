@@ -10,6 +10,9 @@
 //   range   float2 [nl]          (front of the first, back of the last supersegment)
 //                                of each list, (+inf, -inf) when empty: a list the
 //                                ray crosses entirely before or after it needs no search
+//   brange  float2 [bh][bw]      the same for blocks of kB x kB lists (min front, max
+//                                back): a ray whose depth range inside a block misses
+//                                it skips the whole block
 // nl = w*h lists, nsp = N_S rounded up to even; unused slots hold f = b = +inf
 // and colour 0.  kappa = -log2(1 - alpha): Eq. 2's 1 - (1 - alpha)^l then is
 // 1 - exp2(-kappa l), one exp2 per supersegment piece, and FP16 storage of
@@ -24,6 +27,7 @@ namespace vdi {
 constexpr int kMaxNz = 64;
 constexpr int kMaxNs = 64;
 constexpr float kErtT = 1.0f / 4096.0f;  // stop once transmittance <= 2^-12
+constexpr int kB = 4;                    // lists per side of a range block
 
 enum { kSearchAlg2 = 0, kSearchBinary = 1, kSearchLinear = 2 };
 
@@ -35,6 +39,8 @@ struct DevVdi {
     const void *colour;
     const uint32_t *grid;
     const float2 *range;
+    const float2 *brange;
+    int bw, bh;
     int T, gw, gh, nz;
     float edges[kMaxNz + 1];  // slab edges in V_O NDC z, edges[0] = -1, edges[nz] = 1
 };
@@ -84,6 +90,7 @@ __device__ __forceinline__ size_t grid_word_base(const DevVdi &v) {
 __device__ __forceinline__ size_t range_word_base(const DevVdi &v) {
     return grid_word_base(v) + (((size_t)v.nz * v.gh * v.gw + 3) & ~(size_t)3);
 }
+__device__ __forceinline__ size_t brange_word_base(const DevVdi &v) { return range_word_base(v) + 2 * (size_t)v.nl; }
 
 template <bool TOUCH>
 __device__ __forceinline__ void mark_colour(const DevVdi &v, uint32_t *bm, int j, int li) {

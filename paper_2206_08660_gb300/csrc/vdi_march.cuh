@@ -234,10 +234,15 @@ __device__ __forceinline__ Seg seg_of(const Ray &r) {
 }
 
 // ---------------------------------------------------------------------------
-// Exact path without empty-space skipping: every list the ray crosses
-// (Amanatides-Woo in V_O NDC, Section 4.1) goes through process_list.
+// Exact path: every list the ray crosses (Amanatides-Woo in V_O NDC, Section
+// 4.1) goes through process_list.  With BLOCKS, the walk first tests each
+// kB x kB block of lists it enters: when the ray's depth range inside the
+// block misses the block's [min front, max back] no list of the block can
+// hold a supersegment the ray meets, and the walk jumps to where the ray
+// leaves the block.  The image is the same; the skipped lists are not
+// counted by the per-ray list counter, so counters use BLOCKS = false.
 // ---------------------------------------------------------------------------
-template <int FMT, int MODE, bool ERT, bool TOUCH = false>
+template <int FMT, int MODE, bool ERT, bool TOUCH = false, bool BLOCKS = false>
 __device__ __forceinline__ void march_exact(const DevVdi &v, Ray &r, Accum &acc, uint32_t &n_lists,
                                             uint32_t &n_segs, uint32_t *bm = nullptr) {
     const float hw = 0.5f * (float)v.w, hh = 0.5f * (float)v.h;
@@ -245,16 +250,52 @@ __device__ __forceinline__ void march_exact(const DevVdi &v, Ray &r, Accum &acc,
     const float dgx = r.dgx * hw, dgy = -r.dgy * hh;
     int ix = min(max((int)floorf(gx0), 0), v.w - 1);
     int iy = min(max((int)floorf(gy0), 0), v.h - 1);
-    const int stx = dgx > 0.f ? 1 : -1, sty = dgy > 0.f ? 1 : -1;
+    const bool px_ = dgx > 0.f, py_ = dgy > 0.f;
+    const int stx = px_ ? 1 : -1, sty = py_ ? 1 : -1;
     const float idgx = 1.f / dgx, idgy = 1.f / dgy;
-    int bx = ix + (dgx > 0.f ? 1 : 0), by = iy + (dgy > 0.f ? 1 : 0);
+    int bx = ix + (px_ ? 1 : 0), by = iy + (py_ ? 1 : 0);
     float sx = (dgx != 0.f) ? ((float)bx - gx0) * idgx : INFINITY;
     float sy = (dgy != 0.f) ? ((float)by - gy0) * idgy : INFINITY;
     const Seg g = seg_of(r);
     int p = -1;
     float s_in = 0.f;
-    const int maxit = v.w + v.h + 2;
+    bool checked = !BLOCKS;
+    const int maxit = v.w + v.h + 2 + (BLOCKS ? (v.bw + v.bh + 2) : 0);
     for (int it = 0; it < maxit; ++it) {
+        if (BLOCKS && !checked) {
+            const int cbx = ix / kB, cby = iy / kB;
+            const int xb = (cbx + (px_ ? 1 : 0)) * kB, yb = (cby + (py_ ? 1 : 0)) * kB;  // exit faces, in lists
+            const float sbx = (dgx != 0.f) ? ((float)xb - gx0) * idgx : INFINITY;
+            const float sby = (dgy != 0.f) ? ((float)yb - gy0) * idgy : INFINITY;
+            const float s_be = fminf(fminf(sbx, sby), 1.f);
+            const float z_a = fmaf(s_in, g.dz, g.z0), z_b = fmaf(s_be, g.dz, g.z0);
+            const float2 br = __ldg(v.brange + (size_t)cby * v.bw + cbx);
+            if (TOUCH) {
+                mark_word<TOUCH>(bm, brange_word_base(v) + 2 * ((size_t)cby * v.bw + cbx));
+                mark_word<TOUCH>(bm, brange_word_base(v) + 2 * ((size_t)cby * v.bw + cbx) + 1);
+            }
+            checked = true;
+            if (fmaxf(z_a, z_b) < br.x || fminf(z_a, z_b) > br.y) {
+                // nothing in this block along the ray: continue from where it leaves the block
+                if (s_be >= 1.f) break;
+                if (sbx <= sby) {
+                    ix = px_ ? xb : xb - 1;
+                    if ((unsigned)ix >= (unsigned)v.w) break;
+                    iy = min(max((int)floorf(fmaf(s_be, dgy, gy0)), cby * kB), min(cby * kB + kB, v.h) - 1);
+                } else {
+                    iy = py_ ? yb : yb - 1;
+                    if ((unsigned)iy >= (unsigned)v.h) break;
+                    ix = min(max((int)floorf(fmaf(s_be, dgx, gx0)), cbx * kB), min(cbx * kB + kB, v.w) - 1);
+                }
+                bx = ix + (px_ ? 1 : 0);
+                by = iy + (py_ ? 1 : 0);
+                sx = (dgx != 0.f) ? ((float)bx - gx0) * idgx : INFINITY;
+                sy = (dgy != 0.f) ? ((float)by - gy0) * idgy : INFINITY;
+                s_in = fmaxf(s_in, s_be);
+                checked = false;
+                continue;
+            }
+        }
         const float s_out = fminf(fminf(sx, sy), 1.f);
         if (s_out > s_in) {
             if (process_list<FMT, MODE, ERT, TOUCH>(v, g, iy * v.w + ix, s_in, s_out, p, acc, n_lists, n_segs, bm))
@@ -266,11 +307,13 @@ __device__ __forceinline__ void march_exact(const DevVdi &v, Ray &r, Accum &acc,
             if ((unsigned)ix >= (unsigned)v.w) break;
             bx += stx;
             sx = ((float)bx - gx0) * idgx;
+            if (BLOCKS && (ix & (kB - 1)) == (px_ ? 0 : kB - 1)) checked = false;  // entered a new block
         } else {
             iy += sty;
             if ((unsigned)iy >= (unsigned)v.h) break;
             by += sty;
             sy = ((float)by - gy0) * idgy;
+            if (BLOCKS && (iy & (kB - 1)) == (py_ ? 0 : kB - 1)) checked = false;
         }
         s_in = fmaxf(s_in, s_out);
     }

@@ -17,7 +17,8 @@
 namespace vdi {
 
 // PATH: 0 = exact walk over every list, 1 = exact walk with empty-space
-// skipping, 2 = ray-subsampled preview (D_R > 1).
+// skipping over the count grid, 2 = ray-subsampled preview (D_R > 1),
+// 3 = exact walk with range-block skipping (the default).
 template <int FMT, int MODE, bool ERT, int WX, int PATH>
 __global__ void __launch_bounds__(256) render_kernel(const ViewConsts c, const DevVdi v, void *out,
                                                      int out_fmt, uint32_t *ray_lists,
@@ -36,6 +37,8 @@ __global__ void __launch_bounds__(256) render_kernel(const ViewConsts c, const D
             march_preview<FMT, MODE, ERT>(v, c, r, acc);
         else if (PATH == 1)
             march_exact_ess<FMT, MODE, ERT>(v, r, acc, nl, nsg);
+        else if (PATH == 3)
+            march_exact<FMT, MODE, ERT, false, true>(v, r, acc, nl, nsg);
         else
             march_exact<FMT, MODE, ERT>(v, r, acc, nl, nsg);
     }
@@ -57,7 +60,7 @@ __global__ void __launch_bounds__(256) touch_kernel(const ViewConsts c, const De
     Accum acc = {0.f, 0.f, 0.f, 1.f};
     uint32_t nl = 0, nsg = 0;
     Ray r;
-    if (setup_ray(c, tr, px, py, lx, ly, r)) march_exact<FMT, kSearchAlg2, true, true>(v, r, acc, nl, nsg, bm);
+    if (setup_ray(c, tr, px, py, lx, ly, r)) march_exact<FMT, kSearchAlg2, true, true, true>(v, r, acc, nl, nsg, bm);
 }
 
 cudaError_t launch_touch(const ViewConsts &c, const DevVdi &v, uint32_t *bm, cudaStream_t st) {
@@ -135,28 +138,30 @@ static cudaError_t launch_ws(const ViewConsts &c, const DevVdi &v, void *out, in
 
 template <int FMT, int MODE>
 static cudaError_t launch_m(const ViewConsts &c, const DevVdi &v, void *out, int out_fmt, uint32_t *rl,
-                            uint32_t *rs, int warp_shape, bool ert, bool ess, cudaStream_t st) {
+                            uint32_t *rs, int warp_shape, bool ert, bool ess, bool blocks, cudaStream_t st) {
     if (c.d_r > 1) return launch_ws<FMT, MODE, true, 2>(c, v, out, out_fmt, rl, rs, warp_shape, st);
     // per-ray counters count whole lists, so they come from the walk over every list
     if (!ert) return launch_ws<FMT, MODE, false, 0>(c, v, out, out_fmt, rl, rs, warp_shape, st);
-    if (ess && !rl && !rs) return launch_ws<FMT, MODE, true, 1>(c, v, out, out_fmt, rl, rs, warp_shape, st);
-    return launch_ws<FMT, MODE, true, 0>(c, v, out, out_fmt, rl, rs, warp_shape, st);
+    if (rl || rs) return launch_ws<FMT, MODE, true, 0>(c, v, out, out_fmt, rl, rs, warp_shape, st);
+    if (ess) return launch_ws<FMT, MODE, true, 1>(c, v, out, out_fmt, rl, rs, warp_shape, st);
+    if (!blocks) return launch_ws<FMT, MODE, true, 0>(c, v, out, out_fmt, rl, rs, warp_shape, st);
+    return launch_ws<FMT, MODE, true, 3>(c, v, out, out_fmt, rl, rs, warp_shape, st);
 }
 
 cudaError_t launch_render(const ViewConsts &c, const DevVdi &v, void *out, int out_fmt, uint32_t *rl, uint32_t *rs,
-                          int search, int warp_shape, bool ert, bool ess, cudaStream_t st) {
+                          int search, int warp_shape, bool ert, bool ess, bool blocks, cudaStream_t st) {
     if (v.fmt == 0) {
         if (search == kSearchBinary)
-            return launch_m<0, kSearchBinary>(c, v, out, out_fmt, rl, rs, warp_shape, ert, ess, st);
+            return launch_m<0, kSearchBinary>(c, v, out, out_fmt, rl, rs, warp_shape, ert, ess, blocks, st);
         if (search == kSearchLinear)
-            return launch_m<0, kSearchLinear>(c, v, out, out_fmt, rl, rs, warp_shape, ert, ess, st);
-        return launch_m<0, kSearchAlg2>(c, v, out, out_fmt, rl, rs, warp_shape, ert, ess, st);
+            return launch_m<0, kSearchLinear>(c, v, out, out_fmt, rl, rs, warp_shape, ert, ess, blocks, st);
+        return launch_m<0, kSearchAlg2>(c, v, out, out_fmt, rl, rs, warp_shape, ert, ess, blocks, st);
     }
     if (search == kSearchBinary)
-        return launch_m<1, kSearchBinary>(c, v, out, out_fmt, rl, rs, warp_shape, ert, ess, st);
+        return launch_m<1, kSearchBinary>(c, v, out, out_fmt, rl, rs, warp_shape, ert, ess, blocks, st);
     if (search == kSearchLinear)
-        return launch_m<1, kSearchLinear>(c, v, out, out_fmt, rl, rs, warp_shape, ert, ess, st);
-    return launch_m<1, kSearchAlg2>(c, v, out, out_fmt, rl, rs, warp_shape, ert, ess, st);
+        return launch_m<1, kSearchLinear>(c, v, out, out_fmt, rl, rs, warp_shape, ert, ess, blocks, st);
+    return launch_m<1, kSearchAlg2>(c, v, out, out_fmt, rl, rs, warp_shape, ert, ess, blocks, st);
 }
 
 cudaError_t launch_upsample(const float4 *lo, int w0, int h0, void *out, int out_fmt, int W, int H,

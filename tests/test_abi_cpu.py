@@ -66,7 +66,7 @@ def test_layout_matches_paper_vdi_sizes(key, w, h):
     assert abs(L.paper_bytes / _golden()[key] - 1) < 2e-3
     # the FP32 device layout holds exactly those bytes too (16 B colour + 8 B depth per slot)
     assert L.depth_bytes + L.colour_bytes == L.paper_bytes
-    assert L.list_bytes == w * h * 8 and L.total_bytes == L.paper_bytes + L.grid_bytes + L.list_bytes
+    assert L.list_bytes == w * h * 8 + (-(-w // 4)) * (-(-h // 4)) * 8 and L.total_bytes == L.paper_bytes + L.grid_bytes + L.list_bytes
     d16 = V.desc(w, h, 20, np.eye(4), np.eye(4), (0, 0, 0), (1, 1, 1), 1.0, V.VDI_F16)
     L16 = V.vdi_layout_bytes(d16)
     assert L16.depth_bytes + L16.colour_bytes == w * h * 20 * 16

@@ -221,3 +221,20 @@ def test_empty_space_skipping_changes_nothing(V, ctx, fmt):
                 assert np.abs(a - b).max() <= 2.0 ** -12, (seed, az)
         finally:
             V.vdi_destroy(vdi)
+
+
+@pytest.mark.parametrize("fmt", [0, 1])
+def test_range_block_skipping_is_bit_identical(V, ctx, fmt):
+    """A 4 x 4 block of lists whose merged depth range the ray misses holds no
+    supersegment the ray meets, so skipping it changes no bit of the image."""
+    for seed, fill in ((6, 0.2), (7, 0.8)):
+        case = random_case(90, 70, 5, seed=seed, fill=fill)
+        vdi = V.vdi_create(ctx, case.gpu_desc(V, fmt), case.vdi.rgba, case.vdi.depth, case.vdi.counts)
+        try:
+            for (az, el, zoom, ortho) in VIEWS:
+                cn = S.orbit_camera(case.bmin, case.bmax, 1.25, az_deg=az, el_deg=el, zoom=zoom, ortho=ortho)
+                a = gpu_render(V, vdi, cn, 85, 66)
+                b = gpu_render(V, vdi, cn, 85, 66, no_blocks=True)
+                assert np.array_equal(a, b), (seed, az)
+        finally:
+            V.vdi_destroy(vdi)
