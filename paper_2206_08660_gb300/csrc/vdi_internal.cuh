@@ -266,4 +266,18 @@ __device__ __forceinline__ int first_dec(const DevVdi &v, int li, float d, int p
 
 __host__ __device__ inline int div_up(int a, int b) { return (a + b - 1) / b; }
 
+// PTX approximate reciprocal and base-2 exponential (documented relative
+// errors of order 2^-23 and 2^-22): the render path needs no IEEE-rounded
+// division, and Eq. 2's opacity 1 - 2^(-kappa l) tolerates a few ulp.
+__device__ __forceinline__ float rcp_fast(float x) {
+    float r;
+    asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
+    return r;
+}
+__device__ __forceinline__ float exp2_fast(float x) {
+    float r;
+    asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
+    return r;
+}
+
 }  // namespace vdi

@@ -27,9 +27,9 @@ struct Ray {
 
 __device__ __forceinline__ void clip_lin(float c0, float c1, float &t0, float &t1) {
     if (c1 > 0.f)
-        t0 = fmaxf(t0, -c0 / c1);
+        t0 = fmaxf(t0, -c0 * rcp_fast(c1));
     else if (c1 < 0.f)
-        t1 = fminf(t1, -c0 / c1);
+        t1 = fminf(t1, -c0 * rcp_fast(c1));
     else if (c0 < 0.f)
         t1 = -INFINITY;
 }
@@ -107,7 +107,7 @@ __device__ __forceinline__ bool setup_ray(const ViewConsts &c, const TileRays &t
     float4 h1 = make_float4(fmaf(t1, b[0], a[0]), fmaf(t1, b[1], a[1]), fmaf(t1, b[2], a[2]),
                             fmaf(t1, b[3], a[3]));
     if (!(h0.w > 0.f) || !(h1.w > 0.f)) return false;
-    const float i0 = 1.f / h0.w, i1 = 1.f / h1.w;
+    const float i0 = rcp_fast(h0.w), i1 = rcp_fast(h1.w);
     const float p0x = h0.x * i0, p0y = h0.y * i0, p0z = h0.z * i0;
     const float p1x = h1.x * i1, p1y = h1.y * i1, p1z = h1.z * i1;
     r.z0 = p0z;
@@ -132,7 +132,7 @@ struct Accum {
 };
 
 __device__ __forceinline__ void add_piece(Accum &acc, float4 col, float len_u) {
-    const float e = exp2f(-col.w * len_u);
+    const float e = exp2_fast(-col.w * len_u);
     const float wgt = acc.T * (1.f - e);
     acc.r = fmaf(wgt, col.x, acc.r);
     acc.g = fmaf(wgt, col.y, acc.g);
@@ -189,7 +189,7 @@ __device__ __forceinline__ bool process_list(const DevVdi &v, const Seg &g, int 
                 mark_colour<TOUCH>(v, bm, j, li);
                 const float4 col = get_colour<FMT>(cc, v, li, j);
                 const float da = fmaf(sa, g.dw, g.w1), db = fmaf(sb, g.dw, g.w1);
-                add_piece(acc, col, g.lw * (sb - sa) / (da * db));
+                add_piece(acc, col, g.lw * (sb - sa) * rcp_fast(da * db));
                 ++n_segs;
                 if (ERT && acc.T <= kErtT) break;
             }
@@ -210,7 +210,7 @@ __device__ __forceinline__ bool process_list(const DevVdi &v, const Seg &g, int 
                 mark_colour<TOUCH>(v, bm, j, li);
                 const float4 col = get_colour<FMT>(cc, v, li, j);
                 const float da = fmaf(sa, g.dw, g.w1), db = fmaf(sb, g.dw, g.w1);
-                add_piece(acc, col, g.lw * (sb - sa) / (da * db));
+                add_piece(acc, col, g.lw * (sb - sa) * rcp_fast(da * db));
                 ++n_segs;
                 if (ERT && acc.T <= kErtT) break;
             }
@@ -226,7 +226,7 @@ __device__ __forceinline__ Seg seg_of(const Ray &r) {
     Seg g;
     g.z0 = r.z0;
     g.dz = r.dz;
-    g.idz = 1.f / r.dz;
+    g.idz = rcp_fast(r.dz);
     g.w1 = r.w1;
     g.dw = r.dw;
     g.lw = r.lw;
@@ -252,7 +252,7 @@ __device__ __forceinline__ void march_exact(const DevVdi &v, Ray &r, Accum &acc,
     int iy = min(max((int)floorf(gy0), 0), v.h - 1);
     const bool px_ = dgx > 0.f, py_ = dgy > 0.f;
     const int stx = px_ ? 1 : -1, sty = py_ ? 1 : -1;
-    const float idgx = 1.f / dgx, idgy = 1.f / dgy;
+    const float idgx = rcp_fast(dgx), idgy = rcp_fast(dgy);
     int bx = ix + (px_ ? 1 : 0), by = iy + (py_ ? 1 : 0);
     float sx = (dgx != 0.f) ? ((float)bx - gx0) * idgx : INFINITY;
     float sy = (dgy != 0.f) ? ((float)by - gy0) * idgy : INFINITY;
@@ -335,7 +335,7 @@ __device__ __forceinline__ void march_exact_ess(const DevVdi &v, Ray &r, Accum &
     const float hw = 0.5f * (float)v.w, hh = 0.5f * (float)v.h;
     const float gx0 = (r.gx0 + 1.f) * hw, gy0 = (1.f - r.gy0) * hh;
     const float dgx = r.dgx * hw, dgy = -r.dgy * hh;
-    const float idgx = 1.f / dgx, idgy = 1.f / dgy;
+    const float idgx = rcp_fast(dgx), idgy = rcp_fast(dgy);
     const int stx = dgx > 0.f ? 1 : -1, sty = dgy > 0.f ? 1 : -1;
     const int T = v.T;
     const Seg g = seg_of(r);
@@ -446,11 +446,11 @@ __device__ __forceinline__ void march_preview(const DevVdi &v, const ViewConsts 
     int cx = min(max((int)floorf(cx0), 0), v.gw - 1);
     int cy = min(max((int)floorf(cy0), 0), v.gh - 1);
     const int stx = dcx > 0.f ? 1 : -1, sty = dcy > 0.f ? 1 : -1;
-    const float idcx = 1.f / dcx, idcy = 1.f / dcy;
+    const float idcx = rcp_fast(dcx), idcy = rcp_fast(dcy);
     int bx = cx + (dcx > 0.f ? 1 : 0), by = cy + (dcy > 0.f ? 1 : 0);
     float sx = (dcx != 0.f) ? ((float)bx - cx0) * idcx : INFINITY;
     float sy = (dcy != 0.f) ? ((float)by - cy0) * idcy : INFINITY;
-    const float z0 = r.z0, dz = r.dz, idz = 1.f / r.dz;
+    const float z0 = r.z0, dz = r.dz, idz = rcp_fast(r.dz);
     const bool inc = dz >= 0.f;
     int cz = 0;
     while (cz + 1 < v.nz && z0 >= v.edges[cz + 1]) ++cz;
@@ -470,8 +470,8 @@ __device__ __forceinline__ void march_preview(const DevVdi &v, const ViewConsts 
             const uint32_t cnt = __ldg(v.grid + ((size_t)cz * v.gh + cy) * v.gw + cx);
             if (cnt) {
                 const int fx = min(v.T, v.w - cx * v.T), fy = min(v.T, v.h - cy * v.T);
-                const float ua = s_in * w0 / fmaf(s_in, dw, w1);
-                const float ub = s_out * w0 / fmaf(s_out, dw, w1);
+                const float ua = s_in * w0 * rcp_fast(fmaf(s_in, dw, w1));
+                const float ub = s_out * w0 * rcp_fast(fmaf(s_out, dw, w1));
                 const float lc = r.lu * (ub - ua);
                 const float want = ((float)cnt / (float)(fx * fy)) * lc * c.cell_scale;
                 // at least one sample per occupied cell; the cap only guards non-finite input
@@ -483,7 +483,7 @@ __device__ __forceinline__ void march_preview(const DevVdi &v, const ViewConsts 
                     const float hy = fmaf(uk, r.h1.y - r.h0.y, r.h0.y);
                     const float hz = fmaf(uk, r.h1.z - r.h0.z, r.h0.z);
                     const float hwc = fmaf(uk, r.h1.w - r.h0.w, r.h0.w);
-                    const float iw = 1.f / hwc;
+                    const float iw = rcp_fast(hwc);
                     const float nx = hx * iw, ny = hy * iw, nz = hz * iw;
                     const int jx = min(max((int)floorf((nx + 1.f) * hw), 0), v.w - 1);
                     const int jy = min(max((int)floorf((1.f - ny) * hh), 0), v.h - 1);
