@@ -516,7 +516,7 @@ def main():
     ablation = {"exact_frames_deg": [wl["frames"][i][0] for i in exact],
                 "default_ms": time_variant(),
                 "ess_ms": time_variant(ess=True),
-                "no_blocks_ms": time_variant(no_blocks=True),
+                "range_blocks_ms": time_variant(blocks=True),
                 "binary_search_ms": time_variant(search=V.VDI_SEARCH_BINARY),
                 "linear_search_ms": time_variant(search=V.VDI_SEARCH_LINEAR),
                 "note": "ms per exact frame, CUDA events, L2 flushed before each repetition"}

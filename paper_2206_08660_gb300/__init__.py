@@ -104,7 +104,7 @@ class VdiServerCounters(C.Structure):
 
 class VdiRenderOpts(C.Structure):
     _fields_ = [("search", C.c_int), ("no_ert", C.c_int), ("ray_lists", C.c_void_p),
-                ("ray_segs", C.c_void_p), ("warp_shape", C.c_int), ("ess", C.c_int), ("no_blocks", C.c_int)]
+                ("ray_segs", C.c_void_p), ("warp_shape", C.c_int), ("ess", C.c_int), ("blocks", C.c_int)]
 
 
 _lib = None
@@ -275,11 +275,11 @@ def vdi_render(vdi, cam: VdiCamera, W, H, d_i, d_r, out, out_fmt=VDI_F32, stream
 
 
 def vdi_render_ex(vdi, cam: VdiCamera, W, H, d_i, d_r, out, out_fmt=VDI_F32, search=VDI_SEARCH_ALG2,
-                  no_ert=False, ray_lists=None, ray_segs=None, warp_shape=-1, ess=False, no_blocks=False,
+                  no_ert=False, ray_lists=None, ray_segs=None, warp_shape=-1, ess=False, blocks=False,
                   stream=None):
     o = VdiRenderOpts()
     o.search, o.no_ert, o.warp_shape, o.ess = int(search), int(bool(no_ert)), int(warp_shape), int(bool(ess))
-    o.no_blocks = int(bool(no_blocks))
+    o.blocks = int(bool(blocks))
     o.ray_lists, o.ray_segs = _dptr(ray_lists), _dptr(ray_segs)
     _check(load().vdi_render_ex(vdi, C.byref(cam), int(W), int(H), int(d_i), int(d_r), _dptr(out),
                                 int(out_fmt), C.byref(o), _stream(stream)))

@@ -551,10 +551,10 @@ VDI_API vdi_status vdi_render_ex(vdi_t *v, const vdi_camera *view, int W, int H,
     const int ws = o.warp_shape >= 0 ? o.warp_shape : default_warp_shape(v, Wr, Hr);
     float4 *lo = nullptr;
     if (d_i == 1) {
-        CK(launch_render(c, v->dv, out_rgba, out_fmt, o.ray_lists, o.ray_segs, o.search, ws, !o.no_ert, o.ess != 0, !o.no_blocks, st));
+        CK(launch_render(c, v->dv, out_rgba, out_fmt, o.ray_lists, o.ray_segs, o.search, ws, !o.no_ert, o.ess != 0, o.blocks != 0, st));
     } else {
         CK(cudaMallocAsync((void **)&lo, (size_t)Wr * Hr * sizeof(float4), st));
-        CK(launch_render(c, v->dv, lo, VDI_F32, o.ray_lists, o.ray_segs, o.search, ws, !o.no_ert, o.ess != 0, !o.no_blocks, st));
+        CK(launch_render(c, v->dv, lo, VDI_F32, o.ray_lists, o.ray_segs, o.search, ws, !o.no_ert, o.ess != 0, o.blocks != 0, st));
         CK(launch_upsample(lo, Wr, Hr, out_rgba, out_fmt, W, H, st));
     }
 done:

@@ -105,9 +105,9 @@ __global__ void __launch_bounds__(256) batch_render_kernel(const BatchParams P) 
                         march_preview<1, kSearchAlg2, true>(v, q.c, ray, acc);
                 } else {
                     if (v.fmt == 0)
-                        march_exact<0, kSearchAlg2, true, false, true>(v, ray, acc, nl, nsg);
+                        march_exact<0, kSearchAlg2, true>(v, ray, acc, nl, nsg);
                     else
-                        march_exact<1, kSearchAlg2, true, false, true>(v, ray, acc, nl, nsg);
+                        march_exact<1, kSearchAlg2, true>(v, ray, acc, nl, nsg);
                 }
             }
             store_px(q.out, q.out_fmt, (size_t)py * q.c.W + px, acc);

@@ -16,9 +16,9 @@
 
 namespace vdi {
 
-// PATH: 0 = exact walk over every list, 1 = exact walk with empty-space
-// skipping over the count grid, 2 = ray-subsampled preview (D_R > 1),
-// 3 = exact walk with range-block skipping (the default).
+// PATH: 0 = exact walk over every list (the default), 1 = exact walk with
+// empty-space skipping over the count grid, 2 = ray-subsampled preview
+// (D_R > 1), 3 = exact walk with range-block skipping.
 template <int FMT, int MODE, bool ERT, int WX, int PATH>
 __global__ void __launch_bounds__(256) render_kernel(const ViewConsts c, const DevVdi v, void *out,
                                                      int out_fmt, uint32_t *ray_lists,
@@ -60,7 +60,7 @@ __global__ void __launch_bounds__(256) touch_kernel(const ViewConsts c, const De
     Accum acc = {0.f, 0.f, 0.f, 1.f};
     uint32_t nl = 0, nsg = 0;
     Ray r;
-    if (setup_ray(c, tr, px, py, lx, ly, r)) march_exact<FMT, kSearchAlg2, true, true, true>(v, r, acc, nl, nsg, bm);
+    if (setup_ray(c, tr, px, py, lx, ly, r)) march_exact<FMT, kSearchAlg2, true, true>(v, r, acc, nl, nsg, bm);
 }
 
 cudaError_t launch_touch(const ViewConsts &c, const DevVdi &v, uint32_t *bm, cudaStream_t st) {

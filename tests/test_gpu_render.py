@@ -233,8 +233,8 @@ def test_range_block_skipping_is_bit_identical(V, ctx, fmt):
         try:
             for (az, el, zoom, ortho) in VIEWS:
                 cn = S.orbit_camera(case.bmin, case.bmax, 1.25, az_deg=az, el_deg=el, zoom=zoom, ortho=ortho)
-                a = gpu_render(V, vdi, cn, 85, 66)
-                b = gpu_render(V, vdi, cn, 85, 66, no_blocks=True)
+                a = gpu_render(V, vdi, cn, 85, 66, blocks=True)
+                b = gpu_render(V, vdi, cn, 85, 66)
                 assert np.array_equal(a, b), (seed, az)
         finally:
             V.vdi_destroy(vdi)
