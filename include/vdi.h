@@ -346,6 +346,30 @@ typedef struct {
 vdi_status vdi_generate(vdi_ctx *ctx, const vdi_volume *vol, const vdi_tf *tf, const vdi_gen_params *params,
                         void *stream, vdi_t **out);
 
+/* ---- render without device allocation -------------------------------------
+ * The paper has no counterpart to this entry point.  It renders exactly what
+ * vdi_render renders, but the low-resolution image of an image-space preview
+ * (d_i > 1) lives in a fixed buffer of this library -- a static device array
+ * of VDI_STATIC_PREVIEW_PIXELS RGBA floats (8 MiB; enough for 1920 x 1080 at
+ * d_i = 2), held on every GPU that loads the library until the process exits
+ * -- so the call performs no device allocation.  It is for callers that
+ * cannot allocate while rendering: an application that has given all device
+ * memory to resident VDIs (a per-frame allocation could fail), a frame loop
+ * that must not wait on an allocator, or a program that allocates only at
+ * start-up.
+ *  - ceil(W/d_i) * ceil(H/d_i) above VDI_STATIC_PREVIEW_PIXELS (with d_i > 1)
+ *    returns VDI_ERR_INVALID_ARG; d_i = 1 needs no buffer.
+ *  - The first call with d_i > 1 on a device looks up the buffer's device
+ *    address (cudaGetSymbolAddress with that device current); make that first
+ *    call before any stream capture.
+ *  - Every call shares the buffer, which keeps the last call's contents (a
+ *    call writes every pixel it reads, so nothing needs clearing): calls that
+ *    overlap on the GPU -- on different streams or from different threads --
+ *    race on it.  Order them on one stream or synchronise between them. */
+#define VDI_STATIC_PREVIEW_PIXELS 524288
+vdi_status vdi_render_preview_static(vdi_t *vdi, const vdi_camera *view, int W, int H, int d_i, int d_r,
+                                     void *out_rgba, int out_fmt, void *stream);
+
 /* ---- diagnostics --------------------------------------------------------
  * Run the device first-supersegment search on a batch of queries against
  * list `list` of `vdi` (Algorithm 2 and the ablation searches).  Device

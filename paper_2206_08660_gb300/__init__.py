@@ -21,13 +21,14 @@ __all__ = [
     "VDI_F32", "VDI_F16", "VDI_MEM_HOST", "VDI_MEM_DEVICE", "VDI_SEARCH_ALG2", "VDI_SEARCH_BINARY",
     "VDI_SEARCH_LINEAR", "VdiError", "VdiCamera", "VdiDesc", "VdiLayout", "VdiRenderOpts", "load",
     "vdi_ctx_create", "vdi_ctx_destroy", "vdi_layout_bytes", "vdi_create", "vdi_download", "vdi_get_layout",
-    "vdi_destroy", "vdi_render", "vdi_render_ex", "vdi_search_first", "vdi_generate", "vdi_touch_bitmap", "vdi_render_batch", "vdi_autotune_batch", "request",
+    "vdi_destroy", "vdi_render", "vdi_render_ex", "vdi_render_preview_static", "VDI_STATIC_PREVIEW_PIXELS", "vdi_search_first", "vdi_generate", "vdi_touch_bitmap", "vdi_render_batch", "vdi_autotune_batch", "request",
     "vdi_server_create", "vdi_server_set_vdi", "vdi_server_submit", "vdi_server_wait", "vdi_server_poll",
     "vdi_server_release", "vdi_server_read", "vdi_server_stats", "vdi_server_destroy", "VdiViewRequest", "VdiTicketInfo",
     "VdiRequest", "VdiBatchOpts", "camera", "desc",
 ]
 
 VDI_F32, VDI_F16 = 0, 1
+VDI_STATIC_PREVIEW_PIXELS = 524288
 VDI_MEM_HOST, VDI_MEM_DEVICE = 0, 1
 VDI_SEARCH_ALG2, VDI_SEARCH_BINARY, VDI_SEARCH_LINEAR = 0, 1, 2
 STATUS = ["VDI_OK", "VDI_ERR_INVALID_ARG", "VDI_ERR_OOM", "VDI_ERR_CUDA", "VDI_ERR_UNSORTED",
@@ -152,6 +153,7 @@ def load(build_if_needed: bool = True):
     _sig(L, "vdi_server_poll", [P, C.c_uint64, P])
     _sig(L, "vdi_server_release", [P, C.c_uint64])
     _sig(L, "vdi_server_read", [P, C.c_uint64, P, C.c_size_t, C.c_int, P])
+    _sig(L, "vdi_render_preview_static", [P, P, C.c_int, C.c_int, C.c_int, C.c_int, P, C.c_int, P])
     _sig(L, "vdi_server_stats", [P, P])
     _sig(L, "vdi_server_destroy", [P], None)
     _lib = L
@@ -272,6 +274,12 @@ def vdi_destroy(vdi):
 def vdi_render(vdi, cam: VdiCamera, W, H, d_i, d_r, out, out_fmt=VDI_F32, stream=None):
     _check(load().vdi_render(vdi, C.byref(cam), int(W), int(H), int(d_i), int(d_r), _dptr(out), int(out_fmt),
                              _stream(stream)))
+
+
+def vdi_render_preview_static(vdi, cam: VdiCamera, W, H, d_i, d_r, out, out_fmt=VDI_F32, stream=None):
+    """vdi_render without device allocation (low-resolution preview image in a static library buffer)."""
+    _check(load().vdi_render_preview_static(vdi, C.byref(cam), int(W), int(H), int(d_i), int(d_r), _dptr(out),
+                                            int(out_fmt), _stream(stream)))
 
 
 def vdi_render_ex(vdi, cam: VdiCamera, W, H, d_i, d_r, out, out_fmt=VDI_F32, search=VDI_SEARCH_ALG2,
