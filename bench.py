@@ -168,6 +168,24 @@ class ClockSampler:
         return {"sm_mhz": float(np.median(sm)), "sm_max_mhz": smax, "reasons": sorted(reasons), "samples": len(sm)}
 
 
+def max_over_ranks(x: float, device=None) -> float:
+    """The largest value of x over the ranks of the default process group (x itself
+    when there is none): the benchmark's time per step is the slowest rank's."""
+    import torch
+    import torch.distributed as dist
+
+    if not (dist.is_available() and dist.is_initialized()) or dist.get_world_size() == 1:
+        return float(x)
+    t = torch.tensor([float(x)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def whole_job_rate(units_per_rank_step: float, step_ms: float, world: int) -> float:
+    """Units per second of the whole job when every rank does the same work per step (weak scaling)."""
+    return world * units_per_rank_step / (step_ms / 1e3)
+
+
 class OracleLeg:
     """The FP64 CPU oracle on the same workload, for the CPU baseline and the
     reference arm.  The oracle renders its own VDI, made by the oracle's FP32
@@ -463,14 +481,10 @@ def main():
     clocks = clk.stop()
     frame_ms = np.array([[evs[k][i][0].elapsed_time(evs[k][i][1]) for i in range(frames_per_step)]
                          for k in range(args.steps)])
-    step_ms = float(frame_ms.sum(axis=1).mean())
-    if world > 1:
-        tt = torch.tensor([step_ms], device=dev)
-        torch.distributed.all_reduce(tt, op=torch.distributed.ReduceOp.MAX)
-        step_ms = float(tt.item())
-    fps = world * frames_per_step / (step_ms / 1e3)
+    step_ms = max_over_ranks(float(frame_ms.sum(axis=1).mean()), dev)
+    fps = whole_job_rate(frames_per_step, step_ms, world)
     rays = sum((-(-W // d)) * (-(-H // d)) for (_, d, _) in wl["frames"])
-    grays = world * rays / (step_ms / 1e3) / 1e9
+    grays = whole_job_rate(rays, step_ms, world) / 1e9
 
     # ---- roofline of the exact-render kernel (frames with d_i = d_r = 1)
     exact = [i for i, (_, d_i, d_r) in enumerate(wl["frames"]) if d_i == 1 and d_r == 1]

@@ -254,7 +254,9 @@ vdi_status vdi_autotune_batch(vdi_ctx *ctx, const vdi_request *reqs, int n, void
  *    `ready_stream` (e.g. the side stream of a vdi_generate) has completed use
  *    the new VDI; the old one is freed when the last batch using it retires;
  *  - results stay in server-owned DEVICE memory until vdi_server_release;
- *  - waits are bounded: vdi_server_wait returns VDI_ERR_TIMEOUT.
+ *  - waits are bounded: vdi_server_wait returns VDI_ERR_TIMEOUT;
+ *  - batches run on streams of the highest priority, so work the caller
+ *    enqueues on default-priority streams (e.g. generation) yields to them.
  * Times are seconds of a host monotonic clock. */
 typedef struct vdi_server vdi_server;
 

@@ -258,8 +258,12 @@ VDI_API vdi_status vdi_server_create(vdi_ctx *ctx, const vdi_server_config *cfg,
     if (!(s->cfg.wait_timeout_s > 0)) s->cfg.wait_timeout_s = 10.0;
     s->slots.resize(cfg->n_slots);
     s->batches.resize(cfg->max_inflight);
+    // batch streams get the highest priority: view requests are latency-bound,
+    // VDI generation on the caller's side stream should yield to them
+    int least = 0, greatest = 0;
+    cudaDeviceGetStreamPriorityRange(&least, &greatest);
     for (auto &b : s->batches) {
-        cudaError_t e = cudaStreamCreateWithFlags(&b.stream, cudaStreamNonBlocking);
+        cudaError_t e = cudaStreamCreateWithPriority(&b.stream, cudaStreamNonBlocking, greatest);
         if (e == cudaSuccess) e = cudaEventCreateWithFlags(&b.done, cudaEventDisableTiming);
         if (e != cudaSuccess) {
             vdi_status r = cuda_fail(e, "server streams");

@@ -1,0 +1,154 @@
+"""Parity at the full workload sizes, in the launch configuration the benchmark
+times, over whole images.
+
+* large: 1024^3 uint8 mixing layer -> GPU vdi_generate 1920x1080, N_S = 20,
+  FP16 colour; renders at 10 and 30 degrees and the previews (D_I, D_R) =
+  (2, 2), (4, 4) at 30 degrees, all 1920x1080 (the benchmark step).
+* plain: 256^3 uint16 value noise -> 1280x720, N_S = 20, tau = 0.01, FP32;
+  views 0/5/15/30 degrees, zoom 1.2.
+* batched: 4 resident VDIs (640x360 N_S=8, 1280x720 N_S=16, 1920x1080 N_S=20,
+  1920x1080 N_S=32) from 512^3 uint8 noise volumes, 64 requests of mixed
+  resolution and deviation U[0, 30] degrees in one persistent launch: every
+  request equals its single-view render, and a sample of them matches the
+  oracle.
+The oracle renders its own VDI, made by its FP32 generation (bit-identical
+supersegments); FP16-colour tolerances apply where the GPU stores FP16.
+"""
+import numpy as np
+import pytest
+
+import bench as B
+import vdi_synth as S
+from helpers import check_tolerance
+
+pytestmark = pytest.mark.gpu
+torch = pytest.importorskip("torch")
+
+
+@pytest.fixture(scope="module")
+def V():
+    import paper_2206_08660_gb300 as V
+
+    V.load()
+    return V
+
+
+@pytest.fixture(scope="module")
+def ctx(V):
+    c = V.vdi_ctx_create(0)
+    yield c
+    V.vdi_ctx_destroy(c)
+
+
+def both(V, ctx, orc, wl, vol, cam_o):
+    bmin, bmax = S.bbox_for_dims(vol.shape)
+    u = 1.0 / max(vol.shape)
+    kn = S.tf_knots(wl["tf"])
+    vd = torch.from_numpy(vol).cuda()
+    vdi = V.vdi_generate(ctx, vd, bmin, bmax, kn, V.camera(cam_o.view, cam_o.proj), wl["w"], wl["h"], wl["ns"],
+                         wl["tau"], u, u, wl["fmt"])
+    torch.cuda.synchronize()
+    del vd
+    rgba, depth, counts = orc.generate(orc.Volume(vol, bmin, bmax), kn, cam_o.view, cam_o.proj, wl["w"], wl["h"],
+                                       wl["ns"], wl["tau"], u, u, fp32=True)
+    sc = orc.Scene(S.VdiArrays(wl["w"], wl["h"], wl["ns"], rgba, depth, counts), cam_o.view, cam_o.proj, bmin, bmax, u)
+    return vdi, sc, bmin, bmax
+
+
+def gpu_frame(V, vdi, cam, W, H, d_i, d_r):
+    out = torch.zeros((H, W, 4), dtype=torch.float16, device="cuda")  # the benchmark's output format
+    V.vdi_render(vdi, V.camera(cam.view, cam.proj), W, H, d_i, d_r, out, V.VDI_F16)
+    torch.cuda.synchronize()
+    return out.float().cpu().numpy().reshape(-1, 4)
+
+
+def oracle_frame(orc, sc, cam, W, H, d_i, d_r):
+    Wr, Hr = -(-W // d_i), -(-H // d_i)
+    if d_r == 1:
+        lo, fl = orc.render_exact(sc, cam.view, cam.proj, Wr, Hr)[0], np.zeros(Wr * Hr, np.uint8)
+    else:
+        lo, fl = orc.render_preview(sc, cam.view, cam.proj, Wr, Hr, d_r)
+    if d_i == 1:
+        return lo, fl == 0
+    hi = orc.upsample(lo, Wr, Hr, W, H)
+    touched = orc.upsample(np.repeat(fl.astype(np.float64)[:, None], 4, 1), Wr, Hr, W, H)[:, 0] > 0
+    return hi, ~touched
+
+
+def test_large_workload_benchmark_frames(V, ctx, orc):
+    wl = B.WORKLOADS["large"]
+    vol = B.make_volume(wl)
+    bmin, bmax = S.bbox_for_dims(vol.shape)
+    cam_o, views = B.cameras(wl, bmin, bmax)
+    vdi, sc, _, _ = both(V, ctx, orc, wl, vol, cam_o)
+    try:
+        for (az, d_i, d_r), cn in zip(wl["frames"], views):
+            if az == 20.0:
+                continue  # 10 and 30 degrees bracket it; keeps the test short
+            got = gpu_frame(V, vdi, cn, wl["W"], wl["H"], d_i, d_r)
+            ref, ok = oracle_frame(orc, sc, cn, wl["W"], wl["H"], d_i, d_r)
+            assert ok.mean() > 0.95 and ref[:, 3].max() > 0.5
+            check_tolerance(got, ref, 1, mask=ok, what=f"large {az} deg D_I={d_i} D_R={d_r}")
+    finally:
+        V.vdi_destroy(vdi)
+
+
+def test_plain_workload_views(V, ctx, orc):
+    wl = B.WORKLOADS["plain"]
+    vol = B.make_volume(wl)
+    bmin, bmax = S.bbox_for_dims(vol.shape)
+    cam_o, views = B.cameras(wl, bmin, bmax)
+    vdi, sc, _, _ = both(V, ctx, orc, wl, vol, cam_o)
+    try:
+        for (az, d_i, d_r), cn in zip(wl["frames"], views):
+            got = gpu_frame(V, vdi, cn, wl["W"], wl["H"], d_i, d_r)
+            ref, ok = oracle_frame(orc, sc, cn, wl["W"], wl["H"], d_i, d_r)
+            assert ref[:, 3].max() > 0.5
+            # FP16 output rounding (<= 2.5e-4) sits well inside the FP32 tolerance
+            check_tolerance(got, ref, 0, what=f"plain {az} deg")
+    finally:
+        V.vdi_destroy(vdi)
+
+
+def test_batched_workload(V, ctx, orc):
+    specs = [(640, 360, 8), (1280, 720, 16), (1920, 1080, 20), (1920, 1080, 32)]
+    kn = S.tf_knots("sparse")
+    vdis, scenes, cams_o = [], [], []
+    try:
+        for k, (w, h, ns) in enumerate(specs):
+            vol = S.value_noise_volume(512, seed=100 + k, dtype=np.uint8)
+            bmin, bmax = S.bbox_for_dims(vol.shape)
+            cam_o = S.orbit_camera(bmin, bmax, w / h, az_deg=90.0 * k, el_deg=20.0)
+            wl = dict(w=w, h=h, ns=ns, tau=0.01, fmt=1, tf="sparse")
+            vdi, sc, bmin, bmax = both(V, ctx, orc, wl, vol, cam_o)
+            vdis.append(vdi)
+            scenes.append((sc, bmin, bmax))
+            cams_o.append(90.0 * k)
+        rng = np.random.default_rng(3)
+        res = [(640, 360), (1280, 720), (1920, 1080)]
+        reqs, jobs = [], []
+        for i in range(64):
+            k = int(rng.integers(0, 4))
+            W, H = res[int(rng.integers(0, 3))]
+            sc, bmin, bmax = scenes[k]
+            cam = S.orbit_camera(bmin, bmax, W / H, az_deg=cams_o[k] + float(rng.uniform(-30, 30)), el_deg=20.0)
+            out = torch.zeros((H, W, 4), dtype=torch.float16, device="cuda")
+            reqs.append(V.request(vdis[k], V.camera(cam.view, cam.proj), W, H, 1, 1, out, V.VDI_F16))
+            jobs.append((k, cam, W, H, out))
+        best, ms = V.vdi_autotune_batch(ctx, reqs)
+        for j in jobs:
+            j[4].zero_()
+        V.vdi_render_batch(ctx, reqs)  # autotuned configuration, CUDA graph
+        torch.cuda.synchronize()
+        for i, (k, cam, W, H, out) in enumerate(jobs):
+            alone = torch.zeros_like(out)
+            V.vdi_render(vdis[k], V.camera(cam.view, cam.proj), W, H, 1, 1, alone, V.VDI_F16)
+            torch.cuda.synchronize()
+            assert torch.equal(out, alone), i
+        for i in (0, 17, 42):  # a sample against the oracle
+            k, cam, W, H, out = jobs[i]
+            ref = orc.render_exact(scenes[k][0], cam.view, cam.proj, W, H)[0]
+            check_tolerance(out.float().cpu().numpy(), ref, 1, what=f"batched request {i}")
+    finally:
+        for v in vdis:
+            V.vdi_destroy(v)
