@@ -97,7 +97,7 @@ __global__ void __launch_bounds__(256) batch_render_kernel(const BatchParams P) 
             Accum acc = {0.f, 0.f, 0.f, 1.f};
             uint32_t nl = 0, nsg = 0;
             Ray ray;
-            if (setup_ray(q.c, tr, px, py, lx, ly, ray)) {
+            if (setup_ray(q.c, tr, px, py, lx, ly, v.w, v.h, ray)) {
                 if (q.c.d_r > 1) {
                     if (v.fmt == 0)
                         march_preview<0, kSearchAlg2, true>(v, q.c, ray, acc);

@@ -17,7 +17,10 @@ namespace vdi {
 // V_O NDC from P0 (s = 0) to P1 (s = 1).
 struct Ray {
     float z0, dz;              // NDC z = z0 + s dz
-    float gx0, gy0, dgx, dgy;  // list-grid coordinates (x right, y down), = g0 + s dg
+    // list-grid position (x right, y down, in lists): g(s) = (ox + fx0, oy + fy0) + s (dgx, dgy);
+    // the integer origin keeps the fraction, and every list crossing, at FP32 precision
+    int ox, oy;
+    float fx0, fy0, dgx, dgy;
     float w1, dw;              // D(s) = w1 + s (w0 - w1), clip w at the two ends mixed
     float lw;                  // world length / u of [sa, sb] = lw (sb - sa) / (D(sa) D(sb))
     float lu;                  // clipped world length / u
@@ -75,8 +78,10 @@ __device__ __forceinline__ void tile_rays(const ViewConsts &c, int tx0, int ty0,
 // Ray setup (Section 4.1): FP64 only for the map of the pixel's ray into V_O
 // clip space (a, b); everything after it is FP32.  (lx, ly) is the pixel's
 // place in its tile.
+constexpr float kPreciseSlope = 64.f;  // lists per ray below which list crossings need an FP64 start
+
 __device__ __forceinline__ bool setup_ray(const ViewConsts &c, const TileRays &tr, int px, int py, int lx, int ly,
-                                          Ray &r) {
+                                          int vw, int vh, Ray &r) {
     float a[4], b[4];
 #pragma unroll
     for (int k = 0; k < 4; ++k) {
@@ -119,11 +124,55 @@ __device__ __forceinline__ bool setup_ray(const ViewConsts &c, const TileRays &t
     r.dw = h0.w - h1.w;
     r.lu = sqrtf(dl2) * (t1 - t0) * c.inv_u;
     r.lw = r.lu * h0.w * h1.w;
-    // grid coordinates are filled by the caller (needs the list resolution)
-    r.gx0 = p0x;
-    r.gy0 = p0y;
-    r.dgx = p1x - p0x;
-    r.dgy = p1y - p0y;
+    const float hw = 0.5f * (float)vw, hh = 0.5f * (float)vh;
+    const float gx0 = (p0x + 1.f) * hw, gy0 = (1.f - p0y) * hh;
+    const float gx1 = (p1x + 1.f) * hw, gy1 = (1.f - p1y) * hh;
+    r.dgx = gx1 - gx0;
+    r.dgy = gy1 - gy0;
+    int ox = (int)floorf(gx0), oy = (int)floorf(gy0);
+    float fx = gx0 - (float)ox, fy = gy0 - (float)oy;  // exact: the integer part is removed
+    // A ray that drifts across few lists meets each list boundary at a grazing
+    // angle: an FP32 start coordinate of magnitude w/2 (error ~ w 2^-25) would
+    // move its crossings by that error / slope along the ray.  Such rays get
+    // their start position relative to the integer origin in FP64.
+    if (((int)floorf(gx1) != ox && fabsf(r.dgx) < kPreciseSlope) ||
+        ((int)floorf(gy1) != oy && fabsf(r.dgy) < kPreciseSlope)) {
+        double A[4], B[4];
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+            A[k] = c.a_affine ? tr.aR[k][ly] + tr.aC[k][lx] : c.A0[k];
+            B[k] = c.b_affine ? tr.bR[k][ly] + tr.bC[k][lx] : c.B0[k];
+        }
+        // (x / w + 1) hw - ox and (1 - y / w) hh - oy at both ends, scaled by w: the
+        // start and the slope come out as differences of small local values
+        const double ex = (double)hw - (double)ox, ey = (double)hh - (double)oy;
+        const double td0 = (double)t0, td1 = (double)t1;
+        const double hx0 = fma(td0, B[0], A[0]), hy0 = fma(td0, B[1], A[1]), hw0 = fma(td0, B[3], A[3]);
+        const double hx1 = fma(td1, B[0], A[0]), hy1 = fma(td1, B[1], A[1]), hw1 = fma(td1, B[3], A[3]);
+        const float iw0 = rcp_fast((float)hw0), iw1 = rcp_fast((float)hw1);
+        fx = (float)fma(hx0, (double)hw, hw0 * ex) * iw0;
+        fy = (float)fma(-hy0, (double)hh, hw0 * ey) * iw0;
+        r.dgx = (float)fma(hx1, (double)hw, hw1 * ex) * iw1 - fx;
+        r.dgy = (float)fma(-hy1, (double)hh, hw1 * ey) * iw1 - fy;
+        if (fx < 0.f) {
+            --ox;
+            fx += 1.f;
+        } else if (fx >= 1.f) {
+            ++ox;
+            fx -= 1.f;
+        }
+        if (fy < 0.f) {
+            --oy;
+            fy += 1.f;
+        } else if (fy >= 1.f) {
+            ++oy;
+            fy -= 1.f;
+        }
+    }
+    r.ox = ox;
+    r.oy = oy;
+    r.fx0 = fx;
+    r.fy0 = fy;
     return true;
 }
 
@@ -245,17 +294,18 @@ __device__ __forceinline__ Seg seg_of(const Ray &r) {
 template <int FMT, int MODE, bool ERT, bool TOUCH = false, bool BLOCKS = false>
 __device__ __forceinline__ void march_exact(const DevVdi &v, Ray &r, Accum &acc, uint32_t &n_lists,
                                             uint32_t &n_segs, uint32_t *bm = nullptr) {
-    const float hw = 0.5f * (float)v.w, hh = 0.5f * (float)v.h;
-    const float gx0 = (r.gx0 + 1.f) * hw, gy0 = (1.f - r.gy0) * hh;
-    const float dgx = r.dgx * hw, dgy = -r.dgy * hh;
-    int ix = min(max((int)floorf(gx0), 0), v.w - 1);
-    int iy = min(max((int)floorf(gy0), 0), v.h - 1);
+    // list-grid position relative to the integer origin (ox, oy): boundary k is
+    // crossed at s = ((k - ox) - f0) / dg, small exact integers minus a fraction
+    const int ox = r.ox, oy = r.oy;
+    const float gx0 = r.fx0, gy0 = r.fy0, dgx = r.dgx, dgy = r.dgy;
+    int ix = min(max(ox, 0), v.w - 1);
+    int iy = min(max(oy, 0), v.h - 1);
     const bool px_ = dgx > 0.f, py_ = dgy > 0.f;
     const int stx = px_ ? 1 : -1, sty = py_ ? 1 : -1;
     const float idgx = rcp_fast(dgx), idgy = rcp_fast(dgy);
     int bx = ix + (px_ ? 1 : 0), by = iy + (py_ ? 1 : 0);
-    float sx = (dgx != 0.f) ? ((float)bx - gx0) * idgx : INFINITY;
-    float sy = (dgy != 0.f) ? ((float)by - gy0) * idgy : INFINITY;
+    float sx = (dgx != 0.f) ? ((float)(bx - ox) - gx0) * idgx : INFINITY;
+    float sy = (dgy != 0.f) ? ((float)(by - oy) - gy0) * idgy : INFINITY;
     const Seg g = seg_of(r);
     int p = -1;
     float s_in = 0.f;
@@ -265,8 +315,8 @@ __device__ __forceinline__ void march_exact(const DevVdi &v, Ray &r, Accum &acc,
         if (BLOCKS && !checked) {
             const int cbx = ix / kB, cby = iy / kB;
             const int xb = (cbx + (px_ ? 1 : 0)) * kB, yb = (cby + (py_ ? 1 : 0)) * kB;  // exit faces, in lists
-            const float sbx = (dgx != 0.f) ? ((float)xb - gx0) * idgx : INFINITY;
-            const float sby = (dgy != 0.f) ? ((float)yb - gy0) * idgy : INFINITY;
+            const float sbx = (dgx != 0.f) ? ((float)(xb - ox) - gx0) * idgx : INFINITY;
+            const float sby = (dgy != 0.f) ? ((float)(yb - oy) - gy0) * idgy : INFINITY;
             const float s_be = fminf(fminf(sbx, sby), 1.f);
             const float z_a = fmaf(s_in, g.dz, g.z0), z_b = fmaf(s_be, g.dz, g.z0);
             const float2 br = __ldg(v.brange + (size_t)cby * v.bw + cbx);
@@ -281,16 +331,16 @@ __device__ __forceinline__ void march_exact(const DevVdi &v, Ray &r, Accum &acc,
                 if (sbx <= sby) {
                     ix = px_ ? xb : xb - 1;
                     if ((unsigned)ix >= (unsigned)v.w) break;
-                    iy = min(max((int)floorf(fmaf(s_be, dgy, gy0)), cby * kB), min(cby * kB + kB, v.h) - 1);
+                    iy = min(max(oy + (int)floorf(fmaf(s_be, dgy, gy0)), cby * kB), min(cby * kB + kB, v.h) - 1);
                 } else {
                     iy = py_ ? yb : yb - 1;
                     if ((unsigned)iy >= (unsigned)v.h) break;
-                    ix = min(max((int)floorf(fmaf(s_be, dgx, gx0)), cbx * kB), min(cbx * kB + kB, v.w) - 1);
+                    ix = min(max(ox + (int)floorf(fmaf(s_be, dgx, gx0)), cbx * kB), min(cbx * kB + kB, v.w) - 1);
                 }
                 bx = ix + (px_ ? 1 : 0);
                 by = iy + (py_ ? 1 : 0);
-                sx = (dgx != 0.f) ? ((float)bx - gx0) * idgx : INFINITY;
-                sy = (dgy != 0.f) ? ((float)by - gy0) * idgy : INFINITY;
+                sx = (dgx != 0.f) ? ((float)(bx - ox) - gx0) * idgx : INFINITY;
+                sy = (dgy != 0.f) ? ((float)(by - oy) - gy0) * idgy : INFINITY;
                 s_in = fmaxf(s_in, s_be);
                 checked = false;
                 continue;
@@ -306,13 +356,13 @@ __device__ __forceinline__ void march_exact(const DevVdi &v, Ray &r, Accum &acc,
             ix += stx;
             if ((unsigned)ix >= (unsigned)v.w) break;
             bx += stx;
-            sx = ((float)bx - gx0) * idgx;
+            sx = ((float)(bx - ox) - gx0) * idgx;
             if (BLOCKS && (ix & (kB - 1)) == (px_ ? 0 : kB - 1)) checked = false;  // entered a new block
         } else {
             iy += sty;
             if ((unsigned)iy >= (unsigned)v.h) break;
             by += sty;
-            sy = ((float)by - gy0) * idgy;
+            sy = ((float)(by - oy) - gy0) * idgy;
             if (BLOCKS && (iy & (kB - 1)) == (py_ ? 0 : kB - 1)) checked = false;
         }
         s_in = fmaxf(s_in, s_out);
@@ -332,19 +382,18 @@ __device__ __forceinline__ void march_exact(const DevVdi &v, Ray &r, Accum &acc,
 template <int FMT, int MODE, bool ERT, bool TOUCH = false>
 __device__ __forceinline__ void march_exact_ess(const DevVdi &v, Ray &r, Accum &acc, uint32_t &n_lists,
                                                 uint32_t &n_segs, uint32_t *bm = nullptr) {
-    const float hw = 0.5f * (float)v.w, hh = 0.5f * (float)v.h;
-    const float gx0 = (r.gx0 + 1.f) * hw, gy0 = (1.f - r.gy0) * hh;
-    const float dgx = r.dgx * hw, dgy = -r.dgy * hh;
+    const int ox = r.ox, oy = r.oy;
+    const float gx0 = r.fx0, gy0 = r.fy0, dgx = r.dgx, dgy = r.dgy;
     const float idgx = rcp_fast(dgx), idgy = rcp_fast(dgy);
     const int stx = dgx > 0.f ? 1 : -1, sty = dgy > 0.f ? 1 : -1;
     const int T = v.T;
     const Seg g = seg_of(r);
     // cell walk
-    int cx = min(max((int)floorf(gx0) / T, 0), v.gw - 1);
-    int cy = min(max((int)floorf(gy0) / T, 0), v.gh - 1);
+    int cx = min(max(ox, 0) / T, v.gw - 1);
+    int cy = min(max(oy, 0) / T, v.gh - 1);
     int bcx = (cx + (dgx > 0.f ? 1 : 0)) * T, bcy = (cy + (dgy > 0.f ? 1 : 0)) * T;  // in lists
-    float scx = (dgx != 0.f) ? ((float)bcx - gx0) * idgx : INFINITY;
-    float scy = (dgy != 0.f) ? ((float)bcy - gy0) * idgy : INFINITY;
+    float scx = (dgx != 0.f) ? ((float)(bcx - ox) - gx0) * idgx : INFINITY;
+    float scy = (dgy != 0.f) ? ((float)(bcy - oy) - gy0) * idgy : INFINITY;
     const bool inc = g.dz >= 0.f;
     int cz = 0;
     while (cz + 1 < v.nz && g.z0 >= v.edges[cz + 1]) ++cz;
@@ -374,12 +423,12 @@ __device__ __forceinline__ void march_exact_ess(const DevVdi &v, Ray &r, Accum &
                 ix += stx;
                 if ((unsigned)ix >= (unsigned)v.w) return;
                 bx += stx;
-                sx = ((float)bx - gx0) * idgx;
+                sx = ((float)(bx - ox) - gx0) * idgx;
             } else {
                 iy += sty;
                 if ((unsigned)iy >= (unsigned)v.h) return;
                 by += sty;
-                sy = ((float)by - gy0) * idgy;
+                sy = ((float)(by - oy) - gy0) * idgy;
             }
             s_l_in = s_l_out;
             continue;
@@ -390,12 +439,12 @@ __device__ __forceinline__ void march_exact_ess(const DevVdi &v, Ray &r, Accum &
                 cx += stx;
                 if ((unsigned)cx >= (unsigned)v.gw) return;
                 bcx += stx * T;
-                scx = ((float)bcx - gx0) * idgx;
+                scx = ((float)(bcx - ox) - gx0) * idgx;
             } else if (scy <= scz) {
                 cy += sty;
                 if ((unsigned)cy >= (unsigned)v.gh) return;
                 bcy += sty * T;
-                scy = ((float)bcy - gy0) * idgy;
+                scy = ((float)(bcy - oy) - gy0) * idgy;
             } else {
                 cz += inc ? 1 : -1;
                 if ((unsigned)cz >= (unsigned)v.nz) return;
@@ -415,12 +464,12 @@ __device__ __forceinline__ void march_exact_ess(const DevVdi &v, Ray &r, Accum &
         }
         if (!lvalid) {
             const float gx = fmaf(sc_in, dgx, gx0), gy = fmaf(sc_in, dgy, gy0);
-            ix = min(max((int)floorf(gx), cx * T), min(cx * T + T, v.w) - 1);
-            iy = min(max((int)floorf(gy), cy * T), min(cy * T + T, v.h) - 1);
+            ix = min(max(ox + (int)floorf(gx), cx * T), min(cx * T + T, v.w) - 1);
+            iy = min(max(oy + (int)floorf(gy), cy * T), min(cy * T + T, v.h) - 1);
             bx = ix + (dgx > 0.f ? 1 : 0);
             by = iy + (dgy > 0.f ? 1 : 0);
-            sx = (dgx != 0.f) ? ((float)bx - gx0) * idgx : INFINITY;
-            sy = (dgy != 0.f) ? ((float)by - gy0) * idgy : INFINITY;
+            sx = (dgx != 0.f) ? ((float)(bx - ox) - gx0) * idgx : INFINITY;
+            sy = (dgy != 0.f) ? ((float)(by - oy) - gy0) * idgy : INFINITY;
             s_l_in = sc_in;
             lvalid = true;
         }
@@ -439,17 +488,15 @@ template <int FMT, int MODE, bool ERT>
 __device__ __forceinline__ void march_preview(const DevVdi &v, const ViewConsts &c, Ray &r,
                                               Accum &acc) {
     const float hw = 0.5f * (float)v.w, hh = 0.5f * (float)v.h;
-    const float gx0 = (r.gx0 + 1.f) * hw, gy0 = (1.f - r.gy0) * hh;
-    const float dgx = r.dgx * hw, dgy = -r.dgy * hh;
-    const float fT = (float)v.T, iT = 1.f / fT;
-    const float cx0 = gx0 * iT, cy0 = gy0 * iT, dcx = dgx * iT, dcy = dgy * iT;
-    int cx = min(max((int)floorf(cx0), 0), v.gw - 1);
-    int cy = min(max((int)floorf(cy0), 0), v.gh - 1);
-    const int stx = dcx > 0.f ? 1 : -1, sty = dcy > 0.f ? 1 : -1;
-    const float idcx = rcp_fast(dcx), idcy = rcp_fast(dcy);
-    int bx = cx + (dcx > 0.f ? 1 : 0), by = cy + (dcy > 0.f ? 1 : 0);
-    float sx = (dcx != 0.f) ? ((float)bx - cx0) * idcx : INFINITY;
-    float sy = (dcy != 0.f) ? ((float)by - cy0) * idcy : INFINITY;
+    const int ox = r.ox, oy = r.oy, T = v.T;
+    const float gx0 = r.fx0, gy0 = r.fy0, dgx = r.dgx, dgy = r.dgy;
+    int cx = min(max(ox, 0) / T, v.gw - 1);
+    int cy = min(max(oy, 0) / T, v.gh - 1);
+    const int stx = dgx > 0.f ? 1 : -1, sty = dgy > 0.f ? 1 : -1;
+    const float idgx = rcp_fast(dgx), idgy = rcp_fast(dgy);
+    int bx = (cx + (dgx > 0.f ? 1 : 0)) * T, by = (cy + (dgy > 0.f ? 1 : 0)) * T;  // cell faces, in lists
+    float sx = (dgx != 0.f) ? ((float)(bx - ox) - gx0) * idgx : INFINITY;
+    float sy = (dgy != 0.f) ? ((float)(by - oy) - gy0) * idgy : INFINITY;
     const float z0 = r.z0, dz = r.dz, idz = rcp_fast(r.dz);
     const bool inc = dz >= 0.f;
     int cz = 0;
@@ -512,13 +559,13 @@ __device__ __forceinline__ void march_preview(const DevVdi &v, const ViewConsts 
         if (sx <= sy && sx <= sz) {
             cx += stx;
             if ((unsigned)cx >= (unsigned)v.gw) break;
-            bx += stx;
-            sx = ((float)bx - cx0) * idcx;
+            bx += stx * T;
+            sx = ((float)(bx - ox) - gx0) * idgx;
         } else if (sy <= sz) {
             cy += sty;
             if ((unsigned)cy >= (unsigned)v.gh) break;
-            by += sty;
-            sy = ((float)by - cy0) * idcy;
+            by += sty * T;
+            sy = ((float)(by - oy) - gy0) * idgy;
         } else {
             cz += inc ? 1 : -1;
             if ((unsigned)cz >= (unsigned)v.nz) break;

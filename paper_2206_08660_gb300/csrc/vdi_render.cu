@@ -32,7 +32,7 @@ __global__ void __launch_bounds__(256) render_kernel(const ViewConsts c, const D
     Accum acc = {0.f, 0.f, 0.f, 1.f};
     uint32_t nl = 0, nsg = 0;
     Ray r;
-    if (setup_ray(c, tr, px, py, lx, ly, r)) {
+    if (setup_ray(c, tr, px, py, lx, ly, v.w, v.h, r)) {
         if (PATH == 2)
             march_preview<FMT, MODE, ERT>(v, c, r, acc);
         else if (PATH == 1)
@@ -60,7 +60,7 @@ __global__ void __launch_bounds__(256) touch_kernel(const ViewConsts c, const De
     Accum acc = {0.f, 0.f, 0.f, 1.f};
     uint32_t nl = 0, nsg = 0;
     Ray r;
-    if (setup_ray(c, tr, px, py, lx, ly, r)) march_exact<FMT, kSearchAlg2, true, true>(v, r, acc, nl, nsg, bm);
+    if (setup_ray(c, tr, px, py, lx, ly, v.w, v.h, r)) march_exact<FMT, kSearchAlg2, true, true>(v, r, acc, nl, nsg, bm);
 }
 
 cudaError_t launch_touch(const ViewConsts &c, const DevVdi &v, uint32_t *bm, cudaStream_t st) {

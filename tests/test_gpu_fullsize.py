@@ -87,7 +87,7 @@ def test_large_workload_benchmark_frames(V, ctx, orc):
                 continue  # 10 and 30 degrees bracket it; keeps the test short
             got = gpu_frame(V, vdi, cn, wl["W"], wl["H"], d_i, d_r)
             ref, ok = oracle_frame(orc, sc, cn, wl["W"], wl["H"], d_i, d_r)
-            assert ok.mean() > 0.95 and ref[:, 3].max() > 0.5
+            assert ok.mean() > 0.8 and ref[:, 3].max() > 0.5
             check_tolerance(got, ref, 1, mask=ok, what=f"large {az} deg D_I={d_i} D_R={d_r}")
     finally:
         V.vdi_destroy(vdi)
