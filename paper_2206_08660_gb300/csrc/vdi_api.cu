@@ -127,6 +127,8 @@ vdi_status check_desc(const vdi_desc *d, vdi_layout *L) {
         return fail(VDI_ERR_INVALID_ARG, "non-finite V_O matrices");
     const size_t nl = (size_t)d->w * d->h;
     const int nsp = (d->n_s + 1) & ~1;
+    if (nl * (size_t)nsp >= ((size_t)1 << 31))
+        return fail(VDI_ERR_UNSUPPORTED, "%dx%d lists x %d slots exceed 2^31 slot records", d->w, d->h, nsp);
     L->n_s_stored = nsp;
     L->depth_bytes = nl * nsp * 2 * sizeof(float);
     L->colour_bytes = nl * nsp * (d->colour_fmt == VDI_F32 ? 16 : 8);
@@ -376,6 +378,7 @@ vdi_status alloc_vdi(vdi_ctx *ctx, const vdi_desc *desc, cudaStream_t stream, vd
     d.nsp = L.n_s_stored;
     d.fmt = desc->colour_fmt;
     d.nl = (long long)desc->w * desc->h;
+    d.nl32 = (int)d.nl;
     d.T = v->desc.grid_tile;
     d.gw = L.grid_w;
     d.gh = L.grid_h;

@@ -35,6 +35,7 @@ struct DevVdi {
     int w, h, ns, nsp;
     int fmt;  // 0 = F32, 1 = F16
     long long nl;
+    int nl32;  // nl as int: slot-plane offsets k * nl32 + li fit 32 bits (checked when the VDI is built)
     const float4 *depth;
     const void *colour;
     const uint32_t *grid;
@@ -110,14 +111,14 @@ struct PairCache {
 };
 
 __device__ __forceinline__ float4 ld_depth_pair(const DevVdi &v, int k, int li) {
-    return __ldg(v.depth + (size_t)k * v.nl + li);
+    return __ldg(v.depth + (k * v.nl32 + li));
 }
 __device__ __forceinline__ float ld_back(const DevVdi &v, int j, int li) {
-    const float *p = reinterpret_cast<const float *>(v.depth + (size_t)(j >> 1) * v.nl + li);
+    const float *p = reinterpret_cast<const float *>(v.depth + ((j >> 1) * v.nl32 + li));
     return __ldg(p + 2 * (j & 1) + 1);
 }
 __device__ __forceinline__ float ld_front(const DevVdi &v, int j, int li) {
-    const float *p = reinterpret_cast<const float *>(v.depth + (size_t)(j >> 1) * v.nl + li);
+    const float *p = reinterpret_cast<const float *>(v.depth + ((j >> 1) * v.nl32 + li));
     return __ldg(p + 2 * (j & 1));
 }
 __device__ __forceinline__ void get_fb(PairCache &pc, const DevVdi &v, int li, int j, float &f,
@@ -141,11 +142,11 @@ struct ColourCache {
 template <int FMT>
 __device__ __forceinline__ float4 get_colour(ColourCache<FMT> &cc, const DevVdi &v, int li, int j) {
     if (FMT == 0) {
-        return __ldg(reinterpret_cast<const float4 *>(v.colour) + (size_t)j * v.nl + li);
+        return __ldg(reinterpret_cast<const float4 *>(v.colour) + (j * v.nl32 + li));
     } else {
         int k = j >> 1;
         if (k != cc.k) {
-            cc.q = __ldg(reinterpret_cast<const uint4 *>(v.colour) + (size_t)k * v.nl + li);
+            cc.q = __ldg(reinterpret_cast<const uint4 *>(v.colour) + (k * v.nl32 + li));
             cc.k = k;
         }
         unsigned u0 = (j & 1) ? cc.q.z : cc.q.x;

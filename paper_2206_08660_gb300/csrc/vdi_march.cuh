@@ -304,8 +304,11 @@ __device__ __forceinline__ void march_exact(const DevVdi &v, Ray &r, Accum &acc,
     const int stx = px_ ? 1 : -1, sty = py_ ? 1 : -1;
     const float idgx = rcp_fast(dgx), idgy = rcp_fast(dgy);
     int bx = ix + (px_ ? 1 : 0), by = iy + (py_ ? 1 : 0);
-    float sx = (dgx != 0.f) ? ((float)(bx - ox) - gx0) * idgx : INFINITY;
-    float sy = (dgy != 0.f) ? ((float)(by - oy) - gy0) * idgy : INFINITY;
+    // crossing of the next boundary = (offset of the boundary from the origin) * idg - f0 * idg
+    const float fsx = (float)stx, fsy = (float)sty, cx0 = -gx0 * idgx, cy0 = -gy0 * idgy;
+    float fbx = (float)(bx - ox), fby = (float)(by - oy);
+    float sx = (dgx != 0.f) ? fmaf(fbx, idgx, cx0) : INFINITY;
+    float sy = (dgy != 0.f) ? fmaf(fby, idgy, cy0) : INFINITY;
     const Seg g = seg_of(r);
     int p = -1;
     float s_in = 0.f;
@@ -315,8 +318,8 @@ __device__ __forceinline__ void march_exact(const DevVdi &v, Ray &r, Accum &acc,
         if (BLOCKS && !checked) {
             const int cbx = ix / kB, cby = iy / kB;
             const int xb = (cbx + (px_ ? 1 : 0)) * kB, yb = (cby + (py_ ? 1 : 0)) * kB;  // exit faces, in lists
-            const float sbx = (dgx != 0.f) ? ((float)(xb - ox) - gx0) * idgx : INFINITY;
-            const float sby = (dgy != 0.f) ? ((float)(yb - oy) - gy0) * idgy : INFINITY;
+            const float sbx = (dgx != 0.f) ? fmaf((float)(xb - ox), idgx, cx0) : INFINITY;
+            const float sby = (dgy != 0.f) ? fmaf((float)(yb - oy), idgy, cy0) : INFINITY;
             const float s_be = fminf(fminf(sbx, sby), 1.f);
             const float z_a = fmaf(s_in, g.dz, g.z0), z_b = fmaf(s_be, g.dz, g.z0);
             const float2 br = __ldg(v.brange + (size_t)cby * v.bw + cbx);
@@ -339,8 +342,10 @@ __device__ __forceinline__ void march_exact(const DevVdi &v, Ray &r, Accum &acc,
                 }
                 bx = ix + (px_ ? 1 : 0);
                 by = iy + (py_ ? 1 : 0);
-                sx = (dgx != 0.f) ? ((float)(bx - ox) - gx0) * idgx : INFINITY;
-                sy = (dgy != 0.f) ? ((float)(by - oy) - gy0) * idgy : INFINITY;
+                fbx = (float)(bx - ox);
+                fby = (float)(by - oy);
+                sx = (dgx != 0.f) ? fmaf(fbx, idgx, cx0) : INFINITY;
+                sy = (dgy != 0.f) ? fmaf(fby, idgy, cy0) : INFINITY;
                 s_in = fmaxf(s_in, s_be);
                 checked = false;
                 continue;
@@ -355,14 +360,14 @@ __device__ __forceinline__ void march_exact(const DevVdi &v, Ray &r, Accum &acc,
         if (sx <= sy) {
             ix += stx;
             if ((unsigned)ix >= (unsigned)v.w) break;
-            bx += stx;
-            sx = ((float)(bx - ox) - gx0) * idgx;
+            fbx += fsx;
+            sx = fmaf(fbx, idgx, cx0);
             if (BLOCKS && (ix & (kB - 1)) == (px_ ? 0 : kB - 1)) checked = false;  // entered a new block
         } else {
             iy += sty;
             if ((unsigned)iy >= (unsigned)v.h) break;
-            by += sty;
-            sy = ((float)(by - oy) - gy0) * idgy;
+            fby += fsy;
+            sy = fmaf(fby, idgy, cy0);
             if (BLOCKS && (iy & (kB - 1)) == (py_ ? 0 : kB - 1)) checked = false;
         }
         s_in = fmaxf(s_in, s_out);
