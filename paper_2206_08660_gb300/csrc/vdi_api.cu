@@ -235,16 +235,34 @@ vdi_status make_view_consts(const vdi_t *v, const vdi_camera *cam, int W, int H,
     // fold the pixel-centre map x = (px + 1/2) 2/W - 1, y = 1 - (py + 1/2) 2/H into
     // affine forms of the integer pixel indices: a = A0' + px Ax' + py Ay'
     const double sx = 2.0 / W, sy = 2.0 / H;
+    double a0[4], ax[4], ay[4], b0[4], bx[4], by[4];
     for (int k = 0; k < 4; ++k) {
-        c->A0[k] = A0[k] + (0.5 * sx - 1.0) * Ax[k] + (1.0 - 0.5 * sy) * Ay[k];
-        c->Ax[k] = sx * Ax[k];
-        c->Ay[k] = -sy * Ay[k];
-        c->B0[k] = B0[k] + (0.5 * sx - 1.0) * Bx[k] + (1.0 - 0.5 * sy) * By[k];
-        c->Bx[k] = sx * Bx[k];
-        c->By[k] = -sy * By[k];
-        c->A0f[k] = (float)c->A0[k];
-        c->B0f[k] = (float)c->B0[k];
+        a0[k] = A0[k] + (0.5 * sx - 1.0) * Ax[k] + (1.0 - 0.5 * sy) * Ay[k];
+        ax[k] = sx * Ax[k];
+        ay[k] = -sy * Ay[k];
+        b0[k] = B0[k] + (0.5 * sx - 1.0) * Bx[k] + (1.0 - 0.5 * sy) * By[k];
+        bx[k] = sx * Bx[k];
+        by[k] = -sy * By[k];
+        c->A0[k] = (float)a0[k];
+        c->Ax[k] = (float)ax[k];
+        c->Ay[k] = (float)ay[k];
+        c->B0[k] = (float)b0[k];
+        c->Bx[k] = (float)bx[k];
+        c->By[k] = (float)by[k];
     }
+    // homogeneous list-grid coordinates: g_x w = hw (x + w), g_y w = hh (w - y)
+    const double hw = 0.5 * v->desc.w, hh = 0.5 * v->desc.h;
+    auto to_grid = [&](const double *q, double *g) {
+        g[0] = hw * (q[0] + q[3]);
+        g[1] = hh * (q[3] - q[1]);
+        g[2] = q[3];
+    };
+    to_grid(a0, c->GA0);
+    to_grid(ax, c->GAx);
+    to_grid(ay, c->GAy);
+    to_grid(b0, c->GB0);
+    to_grid(bx, c->GBx);
+    to_grid(by, c->GBy);
     c->a_affine = a_aff;
     c->b_affine = b_aff;
     for (int k = 0; k < 3; ++k) {
@@ -262,8 +280,8 @@ vdi_status make_view_consts(const vdi_t *v, const vdi_camera *cam, int W, int H,
     c->inv_u = (float)(1.0 / v->desc.length_unit);
     c->W = W;
     c->H = H;
-    c->sx = 2.0 / W;
-    c->sy = 2.0 / H;
+    c->sx = (float)(2.0 / W);
+    c->sy = (float)(2.0 / H);
     c->d_r = d_r;
     c->cell_scale = (float)(v->desc.length_unit / (v->dz_cell * d_r));
     return VDI_OK;

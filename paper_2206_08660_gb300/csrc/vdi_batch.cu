@@ -6,8 +6,8 @@
 // from an atomic counter, so requests of different resolutions, previews and
 // VDIs share the GPU without a launch per view.  Requests with image-space
 // subsampling (D_I > 1) render into a low-resolution scratch image and a second
-// batched kernel upsamples all of them.  The per-request view constants (FP64
-// ray setup, Section 4.1) travel as kernel parameters, so a captured graph is
+// batched kernel upsamples all of them.  The per-request view constants (ray
+// setup, Section 4.1) travel as kernel parameters, so a captured graph is
 // replayed with new views by updating its kernel nodes.
 #include <cuda_runtime.h>
 #include <math.h>
@@ -63,7 +63,6 @@ struct UpParams {
 template <int WX>
 __global__ void __launch_bounds__(256) batch_render_kernel(const BatchParams P) {
     __shared__ int s_tile, s_req;
-    __shared__ TileRays tr;
     for (;;) {
         if (threadIdx.x == 0) {
             const int t = (int)atomicAdd(P.counter, 1u);
@@ -89,7 +88,6 @@ __global__ void __launch_bounds__(256) batch_render_kernel(const BatchParams P) 
         const DevVdi &v = P.vdis[q.vdi];
         const int local = tile - q.tile_base;
         const int tx0 = (local % q.tiles_x) * 32, ty0 = (local / q.tiles_x) * 8;
-        tile_rays(q.c, tx0, ty0, tr);  // synchronises: s_tile / s_req are read before the next write
         int lx, ly;
         tile_offset<WX>(lx, ly);
         const int px = tx0 + lx, py = ty0 + ly;
@@ -97,7 +95,7 @@ __global__ void __launch_bounds__(256) batch_render_kernel(const BatchParams P) 
             Accum acc = {0.f, 0.f, 0.f, 1.f};
             uint32_t nl = 0, nsg = 0;
             Ray ray;
-            if (setup_ray(q.c, tr, px, py, lx, ly, v.w, v.h, ray)) {
+            if (setup_ray(q.c, px, py, v.w, v.h, ray)) {
                 if (q.c.d_r > 1) {
                     if (v.fmt == 0)
                         march_preview<0, kSearchAlg2, true>(v, q.c, ray, acc);
@@ -112,7 +110,7 @@ __global__ void __launch_bounds__(256) batch_render_kernel(const BatchParams P) 
             }
             store_px(q.out, q.out_fmt, (size_t)py * q.c.W + px, acc);
         }
-        __syncthreads();  // the tile's shared ray terms are read until here
+        __syncthreads();  // every thread has read s_tile / s_req before thread 0 writes them again
     }
 }
 

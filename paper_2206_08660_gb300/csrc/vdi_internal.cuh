@@ -54,10 +54,14 @@ struct DevVdi {
 // V_N (O = eye), b is constant for an orthographic one.
 struct ViewConsts {
     // a(px, py) = A0 + px Ax + py Ay for integer pixel indices (pixel centres
-    // and the NDC scale folded in on the host), likewise b
-    double A0[4], Ax[4], Ay[4];
-    double B0[4], Bx[4], By[4];
-    float A0f[4], B0f[4];  // the same constants rounded to FP32, for the non-affine case
+    // and the NDC scale folded in on the host), likewise b; FP32
+    float A0[4], Ax[4], Ay[4];
+    float B0[4], Bx[4], By[4];
+    // the same affine forms in FP64, mapped to homogeneous list-grid
+    // coordinates (hw (x + w), hh (w - y), w) of the VDI's w x h lists
+    // (hw = w / 2, hh = h / 2): the exact start of rays that cross few lists
+    double GA0[3], GAx[3], GAy[3];
+    double GB0[3], GBx[3], GBy[3];
     int a_affine, b_affine;
     float O0[3], Ox[3], Oy[3];
     float D0[3], Dx[3], Dy[3];
@@ -65,7 +69,7 @@ struct ViewConsts {
     float bmin[3], bmax[3];
     float inv_u;        // 1 / length_unit
     int W, H;           // rays rendered (after D_I)
-    double sx, sy;      // 2/W, 2/H
+    float sx, sy;       // 2/W, 2/H
     int d_r;            // ray subsampling (1 = exact path)
     float cell_scale;   // length_unit / (slab view-depth extent * d_r)
 };

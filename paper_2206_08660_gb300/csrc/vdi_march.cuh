@@ -37,59 +37,21 @@ __device__ __forceinline__ void clip_lin(float c0, float c1, float &t0, float &t
         t1 = -INFINITY;
 }
 
-// FP64 affine terms of the rays of one 32 x 8 pixel tile, in shared memory:
-// b(px, py) = (B0 + py By) + px Bx = R[py - ty0] + C[px - tx0] (likewise a), so
-// each ray adds one row and one column term in FP64 instead of evaluating the
-// whole affine form.  [component][row / column] keeps the lane reads
-// conflict-free.
-struct TileRays {
-    double bR[4][8], bC[4][32];
-    double aR[4][8], aC[4][32];
-};
-
-// All threads of the block must call this (it synchronises).
-__device__ __forceinline__ void tile_rays(const ViewConsts &c, int tx0, int ty0, TileRays &tr) {
-    const int t = threadIdx.x;
-    if (c.b_affine) {
-        if (t < 32) {
-            const double dpx = (double)(tx0 + t);
-#pragma unroll
-            for (int k = 0; k < 4; ++k) tr.bC[k][t] = dpx * c.Bx[k];
-        } else if (t < 40) {
-            const double dpy = (double)(ty0 + t - 32);
-#pragma unroll
-            for (int k = 0; k < 4; ++k) tr.bR[k][t - 32] = fma(dpy, c.By[k], c.B0[k]);
-        }
-    }
-    if (c.a_affine) {
-        if (t >= 64 && t < 96) {
-            const double dpx = (double)(tx0 + t - 64);
-#pragma unroll
-            for (int k = 0; k < 4; ++k) tr.aC[k][t - 64] = dpx * c.Ax[k];
-        } else if (t >= 96 && t < 104) {
-            const double dpy = (double)(ty0 + t - 96);
-#pragma unroll
-            for (int k = 0; k < 4; ++k) tr.aR[k][t - 96] = fma(dpy, c.Ay[k], c.A0[k]);
-        }
-    }
-    __syncthreads();
-}
-
-// Ray setup (Section 4.1): FP64 only for the map of the pixel's ray into V_O
-// clip space (a, b); everything after it is FP32.  (lx, ly) is the pixel's
-// place in its tile.
+// Ray setup (Section 4.1): the map of the pixel's ray into V_O clip space
+// (a, b) as FP32 affine forms of the pixel indices; everything after it is
+// FP32, except the exact start of rays that cross few lists (FP64, below).
 constexpr float kPreciseSlope = 64.f;  // lists per ray below which list crossings need an FP64 start
 
-__device__ __forceinline__ bool setup_ray(const ViewConsts &c, const TileRays &tr, int px, int py, int lx, int ly,
-                                          int vw, int vh, Ray &r) {
+__device__ __forceinline__ bool setup_ray(const ViewConsts &c, int px, int py, int vw, int vh, Ray &r) {
+    const float fpx = (float)px, fpy = (float)py;
     float a[4], b[4];
 #pragma unroll
     for (int k = 0; k < 4; ++k) {
-        a[k] = c.a_affine ? (float)(tr.aR[k][ly] + tr.aC[k][lx]) : c.A0f[k];
-        b[k] = c.b_affine ? (float)(tr.bR[k][ly] + tr.bC[k][lx]) : c.B0f[k];
+        a[k] = c.a_affine ? fmaf(fpx, c.Ax[k], fmaf(fpy, c.Ay[k], c.A0[k])) : c.A0[k];
+        b[k] = c.b_affine ? fmaf(fpx, c.Bx[k], fmaf(fpy, c.By[k], c.B0[k])) : c.B0[k];
     }
     // pixel centre in V_N NDC (FP32 is enough for the world-space box clip)
-    const float x = fmaf((float)px + 0.5f, (float)c.sx, -1.f), y = fmaf(-((float)py + 0.5f), (float)c.sy, 1.f);
+    const float x = fmaf(fpx + 0.5f, c.sx, -1.f), y = fmaf(-(fpy + 0.5f), c.sy, 1.f);
     const float xf = x, yf = y;
     float t0 = c.t_lo, t1 = c.t_hi;
 #pragma unroll
@@ -137,23 +99,23 @@ __device__ __forceinline__ bool setup_ray(const ViewConsts &c, const TileRays &t
     // their start position relative to the integer origin in FP64.
     if (((int)floorf(gx1) != ox && fabsf(r.dgx) < kPreciseSlope) ||
         ((int)floorf(gy1) != oy && fabsf(r.dgy) < kPreciseSlope)) {
-        double A[4], B[4];
+        // list-grid homogeneous coordinates G(t) = GA + t GB; the position
+        // relative to the origin is (G_x - ox G_w) / G_w, whose numerator is
+        // c + t d with c, d formed in FP64 before the cancellation
+        const double dpx = (double)px, dpy = (double)py;
+        double ga[3], gb[3];
 #pragma unroll
-        for (int k = 0; k < 4; ++k) {
-            A[k] = c.a_affine ? tr.aR[k][ly] + tr.aC[k][lx] : c.A0[k];
-            B[k] = c.b_affine ? tr.bR[k][ly] + tr.bC[k][lx] : c.B0[k];
+        for (int k = 0; k < 3; ++k) {
+            ga[k] = c.a_affine ? fma(dpx, c.GAx[k], fma(dpy, c.GAy[k], c.GA0[k])) : c.GA0[k];
+            gb[k] = c.b_affine ? fma(dpx, c.GBx[k], fma(dpy, c.GBy[k], c.GB0[k])) : c.GB0[k];
         }
-        // (x / w + 1) hw - ox and (1 - y / w) hh - oy at both ends, scaled by w: the
-        // start and the slope come out as differences of small local values
-        const double ex = (double)hw - (double)ox, ey = (double)hh - (double)oy;
-        const double td0 = (double)t0, td1 = (double)t1;
-        const double hx0 = fma(td0, B[0], A[0]), hy0 = fma(td0, B[1], A[1]), hw0 = fma(td0, B[3], A[3]);
-        const double hx1 = fma(td1, B[0], A[0]), hy1 = fma(td1, B[1], A[1]), hw1 = fma(td1, B[3], A[3]);
-        const float iw0 = rcp_fast((float)hw0), iw1 = rcp_fast((float)hw1);
-        fx = (float)fma(hx0, (double)hw, hw0 * ex) * iw0;
-        fy = (float)fma(-hy0, (double)hh, hw0 * ey) * iw0;
-        r.dgx = (float)fma(hx1, (double)hw, hw1 * ex) * iw1 - fx;
-        r.dgy = (float)fma(-hy1, (double)hh, hw1 * ey) * iw1 - fy;
+        const double dox = (double)ox, doy = (double)oy, td0 = (double)t0, td1 = (double)t1;
+        const double cx = fma(-dox, ga[2], ga[0]), dx = fma(-dox, gb[2], gb[0]);
+        const double cy = fma(-doy, ga[2], ga[1]), dy = fma(-doy, gb[2], gb[1]);
+        fx = (float)fma(td0, dx, cx) * i0;
+        fy = (float)fma(td0, dy, cy) * i0;
+        r.dgx = (float)fma(td1, dx, cx) * i1 - fx;
+        r.dgy = (float)fma(td1, dy, cy) * i1 - fy;
         if (fx < 0.f) {
             --ox;
             fx += 1.f;
@@ -210,16 +172,21 @@ __device__ __forceinline__ bool process_list(const DevVdi &v, const Seg &g, int 
                                              uint32_t *bm) {
     const float d_in = fmaf(s_in, g.dz, g.z0), d_out = fmaf(s_out, g.dz, g.z0);
     ++n_lists;
+    PairCache pc;
+    pc.k = -1;
     {  // the ray crosses this list entirely before its first or after its last supersegment
         const float2 rg = __ldg(v.range + li);
+        if (MODE == kSearchAlg2 && p >= 0) {
+            // the seed's depth record, fetched together with the range
+            pc.k = p >> 1;
+            pc.d = ld_depth_pair(v, pc.k, li);
+        }
         if (TOUCH) {
             mark_word<TOUCH>(bm, range_word_base(v) + 2 * (size_t)li);
             mark_word<TOUCH>(bm, range_word_base(v) + 2 * (size_t)li + 1);
         }
         if (fmaxf(d_in, d_out) < rg.x || fminf(d_in, d_out) > rg.y) return false;
     }
-    PairCache pc;
-    pc.k = -1;
     ColourCache<FMT> cc;
     cc.k = -1;
     int last = -1, first;
@@ -310,7 +277,10 @@ __device__ __forceinline__ void march_exact(const DevVdi &v, Ray &r, Accum &acc,
     float sx = (dgx != 0.f) ? fmaf(fbx, idgx, cx0) : INFINITY;
     float sy = (dgy != 0.f) ? fmaf(fby, idgy, cy0) : INFINITY;
     const Seg g = seg_of(r);
-    int p = -1;
+    // the first list has no previous list: a ray whose depth increases seeds
+    // Algorithm 2 with the front-most supersegment (the one it most likely
+    // meets first); a ray whose depth decreases runs the plain binary search
+    int p = (g.dz >= 0.f) ? 0 : -1;
     float s_in = 0.f;
     bool checked = !BLOCKS;
     const int maxit = v.w + v.h + 2 + (BLOCKS ? (v.bw + v.bh + 2) : 0);

@@ -23,16 +23,14 @@ template <int FMT, int MODE, bool ERT, int WX, int PATH>
 __global__ void __launch_bounds__(256) render_kernel(const ViewConsts c, const DevVdi v, void *out,
                                                      int out_fmt, uint32_t *ray_lists,
                                                      uint32_t *ray_segs) {
-    __shared__ TileRays tr;
     int lx, ly;
     tile_offset<WX>(lx, ly);
-    tile_rays(c, blockIdx.x * 32, blockIdx.y * 8, tr);
     const int px = blockIdx.x * 32 + lx, py = blockIdx.y * 8 + ly;
     if (px >= c.W || py >= c.H) return;
     Accum acc = {0.f, 0.f, 0.f, 1.f};
     uint32_t nl = 0, nsg = 0;
     Ray r;
-    if (setup_ray(c, tr, px, py, lx, ly, v.w, v.h, r)) {
+    if (setup_ray(c, px, py, v.w, v.h, r)) {
         if (PATH == 2)
             march_preview<FMT, MODE, ERT>(v, c, r, acc);
         else if (PATH == 1)
@@ -51,16 +49,14 @@ __global__ void __launch_bounds__(256) render_kernel(const ViewConsts c, const D
 // Instrumented exact render: marks the VDI words the algorithm reads.
 template <int FMT>
 __global__ void __launch_bounds__(256) touch_kernel(const ViewConsts c, const DevVdi v, uint32_t *bm) {
-    __shared__ TileRays tr;
     int lx, ly;
     tile_offset<32>(lx, ly);
-    tile_rays(c, blockIdx.x * 32, blockIdx.y * 8, tr);
     const int px = blockIdx.x * 32 + lx, py = blockIdx.y * 8 + ly;
     if (px >= c.W || py >= c.H) return;
     Accum acc = {0.f, 0.f, 0.f, 1.f};
     uint32_t nl = 0, nsg = 0;
     Ray r;
-    if (setup_ray(c, tr, px, py, lx, ly, v.w, v.h, r)) march_exact<FMT, kSearchAlg2, true, true>(v, r, acc, nl, nsg, bm);
+    if (setup_ray(c, px, py, v.w, v.h, r)) march_exact<FMT, kSearchAlg2, true, true>(v, r, acc, nl, nsg, bm);
 }
 
 cudaError_t launch_touch(const ViewConsts &c, const DevVdi &v, uint32_t *bm, cudaStream_t st) {
