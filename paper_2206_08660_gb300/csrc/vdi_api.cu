@@ -265,6 +265,7 @@ vdi_status make_view_consts(const vdi_t *v, const vdi_camera *cam, int W, int H,
     to_grid(by, c->GBy);
     c->a_affine = a_aff;
     c->b_affine = b_aff;
+    c->frustum_clip = v->box_in_frustum ? 0 : 1;
     for (int k = 0; k < 3; ++k) {
         c->O0[k] = (float)O0[k];
         c->Ox[k] = (float)Ox[k];
@@ -389,6 +390,19 @@ vdi_status alloc_vdi(vdi_ctx *ctx, const vdi_desc *desc, cudaStream_t stream, vd
         return fail(VDI_ERR_INVALID_ARG, "V_O near/far planes are degenerate");
     }
     v->dz_cell = (df - dn) / v->desc.grid_nz;
+    // the V_O frustum clip of a render is redundant when the whole box lies
+    // inside the frustum; the margin covers the FP32 rounding of the clip
+    v->box_in_frustum = true;
+    for (int corner = 0; corner < 8; ++corner) {
+        const double p[4] = {(corner & 1) ? desc->bbox_max[0] : desc->bbox_min[0],
+                             (corner & 2) ? desc->bbox_max[1] : desc->bbox_min[1],
+                             (corner & 4) ? desc->bbox_max[2] : desc->bbox_min[2], 1.0};
+        double q[4];
+        mat4_apply(v->M, p, q);
+        const double lim = q[3] * (1.0 - 1e-4);
+        if (!(q[3] > 0.0) || !(fabs(q[0]) < lim) || !(fabs(q[1]) < lim) || !(fabs(q[2]) < lim))
+            v->box_in_frustum = false;
+    }
     DevVdi &d = v->dv;
     d.w = desc->w;
     d.h = desc->h;

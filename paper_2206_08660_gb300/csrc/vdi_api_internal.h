@@ -19,6 +19,7 @@ struct vdi_t {
     vdi::DevVdi dv{};
     double M[16]{};       // P_O * V_O
     double dz_cell = 0.0; // V_O view-depth extent of one grid slab
+    bool box_in_frustum = false;  // all eight box corners strictly inside V_O's clip volume
     void *depth_mem = nullptr;
     void *colour_mem = nullptr;
     uint32_t *grid_mem = nullptr;

@@ -63,6 +63,7 @@ struct ViewConsts {
     double GA0[3], GAx[3], GAy[3];
     double GB0[3], GBx[3], GBy[3];
     int a_affine, b_affine;
+    int frustum_clip;   // 0 when the volume box lies inside V_O's frustum
     float O0[3], Ox[3], Oy[3];
     float D0[3], Dx[3], Dy[3];
     float t_lo, t_hi;
@@ -142,6 +143,16 @@ struct ColourCache {
     int k;
     uint4 q;
 };
+
+// FP16 colour: fetch the colour record of slot pair k (issued next to the
+// pair's depth record, so that both loads are in flight together)
+template <int FMT>
+__device__ __forceinline__ void fetch_colour_pair(ColourCache<FMT> &cc, const DevVdi &v, int li, int k) {
+    if (FMT == 1 && k != cc.k) {
+        cc.q = __ldg(reinterpret_cast<const uint4 *>(v.colour) + (k * v.nl32 + li));
+        cc.k = k;
+    }
+}
 
 template <int FMT>
 __device__ __forceinline__ float4 get_colour(ColourCache<FMT> &cc, const DevVdi &v, int li, int j) {

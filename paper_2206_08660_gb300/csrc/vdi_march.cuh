@@ -44,31 +44,43 @@ constexpr float kPreciseSlope = 64.f;  // lists per ray below which list crossin
 
 __device__ __forceinline__ bool setup_ray(const ViewConsts &c, int px, int py, int vw, int vh, Ray &r) {
     const float fpx = (float)px, fpy = (float)py;
+    // pixel centre in V_N NDC (FP32 is enough for the world-space box clip)
+    const float x = fmaf(fpx + 0.5f, c.sx, -1.f), y = fmaf(-(fpy + 0.5f), c.sy, 1.f);
+    float t0 = c.t_lo, t1 = c.t_hi;
+    // the volume box first (slabs, one reciprocal per axis): most rays that
+    // miss the volume leave here
+    float dl2 = 0.f;
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+        const float o = fmaf(y, c.Oy[k], fmaf(x, c.Ox[k], c.O0[k]));
+        const float d = fmaf(y, c.Dy[k], fmaf(x, c.Dx[k], c.D0[k]));
+        const float id = rcp_fast(d);
+        float lo = (c.bmin[k] - o) * id, hi = (c.bmax[k] - o) * id;
+        if (d == 0.f) {  // parallel to the slab: inside keeps the ray, outside rejects it
+            hi = INFINITY;
+            lo = (o < c.bmin[k] || o > c.bmax[k]) ? INFINITY : -INFINITY;
+        }
+        t0 = fmaxf(t0, fminf(lo, hi));
+        t1 = fminf(t1, fmaxf(lo, hi));
+        dl2 = fmaf(d, d, dl2);
+    }
+    if (!(t0 < t1)) return false;
     float a[4], b[4];
 #pragma unroll
     for (int k = 0; k < 4; ++k) {
         a[k] = c.a_affine ? fmaf(fpx, c.Ax[k], fmaf(fpy, c.Ay[k], c.A0[k])) : c.A0[k];
         b[k] = c.b_affine ? fmaf(fpx, c.Bx[k], fmaf(fpy, c.By[k], c.B0[k])) : c.B0[k];
     }
-    // pixel centre in V_N NDC (FP32 is enough for the world-space box clip)
-    const float x = fmaf(fpx + 0.5f, c.sx, -1.f), y = fmaf(-(fpy + 0.5f), c.sy, 1.f);
-    const float xf = x, yf = y;
-    float t0 = c.t_lo, t1 = c.t_hi;
+    // V_O's frustum, -w <= x, y, z <= w; skipped when the host found the whole
+    // box inside it (the clip could then never shorten the ray)
+    if (c.frustum_clip) {
 #pragma unroll
-    for (int k = 0; k < 3; ++k) {
-        clip_lin(a[3] + a[k], b[3] + b[k], t0, t1);
-        clip_lin(a[3] - a[k], b[3] - b[k], t0, t1);
+        for (int k = 0; k < 3; ++k) {
+            clip_lin(a[3] + a[k], b[3] + b[k], t0, t1);
+            clip_lin(a[3] - a[k], b[3] - b[k], t0, t1);
+        }
+        if (!(t0 < t1)) return false;
     }
-    float dl2 = 0.f;
-#pragma unroll
-    for (int k = 0; k < 3; ++k) {
-        float o = fmaf(yf, c.Oy[k], fmaf(xf, c.Ox[k], c.O0[k]));
-        float d = fmaf(yf, c.Dy[k], fmaf(xf, c.Dx[k], c.D0[k]));
-        clip_lin(o - c.bmin[k], d, t0, t1);
-        clip_lin(c.bmax[k] - o, -d, t0, t1);
-        dl2 = fmaf(d, d, dl2);
-    }
-    if (!(t0 < t1)) return false;
     float4 h0 = make_float4(fmaf(t0, b[0], a[0]), fmaf(t0, b[1], a[1]), fmaf(t0, b[2], a[2]),
                             fmaf(t0, b[3], a[3]));
     float4 h1 = make_float4(fmaf(t1, b[0], a[0]), fmaf(t1, b[1], a[1]), fmaf(t1, b[2], a[2]),
@@ -174,12 +186,15 @@ __device__ __forceinline__ bool process_list(const DevVdi &v, const Seg &g, int 
     ++n_lists;
     PairCache pc;
     pc.k = -1;
+    ColourCache<FMT> cc;
+    cc.k = -1;
     {  // the ray crosses this list entirely before its first or after its last supersegment
         const float2 rg = __ldg(v.range + li);
         if (MODE == kSearchAlg2 && p >= 0) {
-            // the seed's depth record, fetched together with the range
+            // the seed's depth and colour records, fetched together with the range
             pc.k = p >> 1;
             pc.d = ld_depth_pair(v, pc.k, li);
+            fetch_colour_pair<FMT>(cc, v, li, pc.k);
         }
         if (TOUCH) {
             mark_word<TOUCH>(bm, range_word_base(v) + 2 * (size_t)li);
@@ -187,13 +202,12 @@ __device__ __forceinline__ bool process_list(const DevVdi &v, const Seg &g, int 
         }
         if (fmaxf(d_in, d_out) < rg.x || fminf(d_in, d_out) > rg.y) return false;
     }
-    ColourCache<FMT> cc;
-    cc.k = -1;
     int last = -1, first;
     if (g.dz >= 0.f) {
         first = first_inc<MODE, TOUCH>(v, li, d_in, p, pc, bm);
         for (int j = first; j < v.nsp; ++j) {
             float f, b;
+            fetch_colour_pair<FMT>(cc, v, li, j >> 1);
             get_fb(pc, v, li, j, f, b);
             mark_depth<TOUCH>(v, bm, j, li, 0);
             mark_depth<TOUCH>(v, bm, j, li, 1);
@@ -215,6 +229,7 @@ __device__ __forceinline__ bool process_list(const DevVdi &v, const Seg &g, int 
         first = first_dec<MODE, TOUCH>(v, li, d_in, p, pc, bm);
         for (int j = first; j >= 0; --j) {
             float f, b;
+            fetch_colour_pair<FMT>(cc, v, li, j >> 1);
             get_fb(pc, v, li, j, f, b);
             mark_depth<TOUCH>(v, bm, j, li, 0);
             mark_depth<TOUCH>(v, bm, j, li, 1);

@@ -79,6 +79,32 @@ def test_exact_render_matches_oracle(V, ctx, orc, fmt, seed):
         V.vdi_destroy(vdi)
 
 
+@pytest.mark.parametrize("fmt", [0, 1])
+def test_original_frustum_cuts_the_box(V, ctx, orc, fmt):
+    """V_O zoomed in so that its frustum cuts the volume box: the render clips
+    every ray to V_O's frustum as well as to the box (Section 4.1).  With this
+    zoom some rays of the view along V_O's direction run exactly along a list
+    boundary, where the field is discontinuous and both sides are valid
+    limits; the oracle flags them and they are left out of the comparison."""
+    bmin, bmax = np.zeros(3), np.ones(3)
+    vdi = S.random_vdi(37, 23, 5, seed=11, alpha_range=(0.05, 0.8))
+    cam_o = S.orbit_camera(bmin, bmax, 37 / 23, az_deg=0.0, el_deg=15.0, zoom=1.8)
+    case = Case(vdi, cam_o, bmin, bmax, 0.15)
+    sc = case.oracle_scene(orc)
+    g = V.vdi_create(ctx, case.gpu_desc(V, fmt), vdi.rgba, vdi.depth, vdi.counts)
+    try:
+        for (az, el, zoom, ortho) in VIEWS:
+            W, H = 70, 45
+            cn = S.orbit_camera(bmin, bmax, W / H, az_deg=az, el_deg=el, zoom=zoom, ortho=ortho)
+            ref, _, _, fl = orc.render_exact(sc, cn.view, cn.proj, W, H)
+            got = gpu_render(V, g, cn, W, H)
+            assert ref[:, 3].max() > 0.2, "view shows nothing"
+            assert (fl == 0).mean() > 0.95
+            check_tolerance(got, ref, fmt, mask=fl == 0, what=f"view {az},{el}")
+    finally:
+        V.vdi_destroy(g)
+
+
 def test_counters_bit_exact_on_unflagged_rays(V, ctx, orc):
     case = random_case(29, 17, 4, seed=3, u=0.2)
     sc = case.oracle_scene(orc)
