@@ -103,7 +103,7 @@ typedef struct {
     int no_ert;          /* 1: keep compositing past full opacity (for exact counters) */
     uint32_t *ray_lists; /* nullable device [H'][W']: lists traversed with positive length per ray */
     uint32_t *ray_segs;  /* nullable device [H'][W']: supersegment pieces of positive length per ray */
-    int warp_shape;      /* -1: default/autotuned; 0: 32x1, 1: 16x2, 2: 8x4 pixels per warp */
+    int warp_shape;      /* -1: default (4x8); 0: 32x1, 1: 16x2, 2: 8x4, 3: 4x8 pixels per warp */
     int ess;             /* 1: empty-space skipping over the count grid (Section 4.3): occupied cells
                             only.  Off by default (measured slower on the benchmark workloads); the
                             image is the same up to where early termination lands; per-ray
@@ -209,7 +209,7 @@ vdi_status vdi_render_ex(vdi_t *vdi, const vdi_camera *view, int W, int H, int d
  * path takes scratch from the stream-ordered allocator.  A cached graph lives
  * until vdi_ctx_destroy.  warp_shape = -1 uses the configuration stored by
  * vdi_autotune_batch for batches with the same signature (resolutions,
- * previews, N_S, colour formats), else 32x1. */
+ * previews, N_S, colour formats), else 4x8. */
 enum { VDI_BATCH_MAX_REQUESTS = 64, VDI_BATCH_MAX_VDIS = 8 };
 
 typedef struct {
@@ -221,7 +221,7 @@ typedef struct {
 } vdi_request;
 
 typedef struct {
-    int warp_shape;      /* -1 autotuned/default, 0: 32x1, 1: 16x2, 2: 8x4 pixels per warp */
+    int warp_shape;      /* -1 autotuned/default (4x8), 0: 32x1, 1: 16x2, 2: 8x4, 3: 4x8 pixels per warp */
     int blocks_per_sm;   /* resident blocks per SM of the persistent grid, 0 = occupancy limit */
     int use_graph;       /* 1: replay a cached CUDA graph for this batch shape */
 } vdi_batch_opts;

@@ -576,7 +576,7 @@ VDI_API vdi_status vdi_render_ex(vdi_t *v, const vdi_camera *view, int W, int H,
     vdi_render_opts o = {VDI_SEARCH_ALG2, 0, nullptr, nullptr, -1, 0, 0};
     if (opts) o = *opts;
     if (o.search < 0 || o.search > 2) return fail(VDI_ERR_INVALID_ARG, "search=%d", o.search);
-    if (o.warp_shape < -1 || o.warp_shape > 2) return fail(VDI_ERR_INVALID_ARG, "warp_shape=%d", o.warp_shape);
+    if (o.warp_shape < -1 || o.warp_shape > 3) return fail(VDI_ERR_INVALID_ARG, "warp_shape=%d", o.warp_shape);
     cudaSetDevice(v->ctx->device);
     cudaStream_t st = (cudaStream_t)stream;
     const int Wr = div_up(W, d_i), Hr = div_up(H, d_i);

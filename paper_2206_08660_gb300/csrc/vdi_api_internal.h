@@ -46,6 +46,6 @@ cudaError_t launch_block_range(const DevVdi &v, float2 *brange, cudaStream_t st)
 
 // warp shape used when the caller does not choose one: 32x1 (lanes along a
 // row of lists) unless the autotuner recorded a better one
-inline int default_warp_shape(const vdi_t *, int, int) { return 0; }
+inline int default_warp_shape(const vdi_t *, int, int) { return 3; }  // 4 x 8 pixels per warp
 
 }  // namespace vdi

@@ -150,9 +150,10 @@ __global__ void __launch_bounds__(256) batch_upsample_kernel(const UpParams P) {
 }
 
 static const void *render_fn(int ws) {
+    if (ws == 0) return (const void *)batch_render_kernel<32>;
     if (ws == 1) return (const void *)batch_render_kernel<16>;
     if (ws == 2) return (const void *)batch_render_kernel<8>;
-    return (const void *)batch_render_kernel<32>;
+    return (const void *)batch_render_kernel<4>;
 }
 
 // ---------------------------------------------------------------------------
@@ -405,10 +406,10 @@ vdi_status render_batch(vdi_ctx *ctx, const vdi_request *reqs, int n, const vdi_
             o.warp_shape = it->second.warp_shape;
             if (o.blocks_per_sm == 0) o.blocks_per_sm = it->second.blocks_per_sm;
         } else {
-            o.warp_shape = 0;
+            o.warp_shape = 3;  // 4 x 8 pixels per warp, the single-view default
         }
     }
-    if (o.warp_shape > 2) return fail(VDI_ERR_INVALID_ARG, "warp_shape=%d", o.warp_shape);
+    if (o.warp_shape > 3) return fail(VDI_ERR_INVALID_ARG, "warp_shape=%d", o.warp_shape);
     if (o.blocks_per_sm < 0) return fail(VDI_ERR_INVALID_ARG, "blocks_per_sm=%d", o.blocks_per_sm);
     if (o.use_graph) return enqueue_graph(ctx, reqs, n, pl, o.warp_shape, o.blocks_per_sm, st);
     void *scratch = nullptr;
@@ -460,7 +461,7 @@ VDI_API vdi_status vdi_autotune_batch(vdi_ctx *ctx, const vdi_request *reqs, int
     int occ_max = 1;
     cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ_max, render_fn(0), 256, 0);
     vdi_status s = VDI_OK;
-    for (int ws = 0; ws <= 2 && s == VDI_OK; ++ws)
+    for (int ws = 0; ws <= 3 && s == VDI_OK; ++ws)
         for (int bps = 1; bps <= std::max(1, occ_max) && s == VDI_OK; bps *= 2) {
             vdi_batch_opts o = {ws, bps, 0};
             s = render_batch(ctx, reqs, n, &o, st);  // warm-up

@@ -3,7 +3,7 @@
 // instrumented bytes-touched render and the search diagnostic.
 //
 // One thread per pixel ray.  A block covers 32 x 8 pixels; its eight warps
-// cover 32x1, 16x2 or 8x4 pixels each (the warp shape is a launch choice:
+// cover 32x1, 16x2, 8x4 or 4x8 pixels each (the warp shape is a launch choice:
 // lanes on neighbouring pixels walk neighbouring lists, so their 16-byte
 // depth/colour loads coalesce).
 #include <cuda_fp16.h>
@@ -122,13 +122,15 @@ template <int FMT, int MODE, bool ERT, int PATH>
 static cudaError_t launch_ws(const ViewConsts &c, const DevVdi &v, void *out, int out_fmt, uint32_t *rl,
                              uint32_t *rs, int warp_shape, cudaStream_t st) {
     dim3 grid(div_up(c.W, 32), div_up(c.H, 8)), block(256);
-    // the ablation searches are built with the 32x1 warp shape only
-    if (MODE == kSearchAlg2 && warp_shape == 1)
+    // the ablation searches are built with the default warp shape (4 x 8) only
+    if (MODE == kSearchAlg2 && warp_shape == 0)
+        render_kernel<FMT, MODE, ERT, 32, PATH><<<grid, block, 0, st>>>(c, v, out, out_fmt, rl, rs);
+    else if (MODE == kSearchAlg2 && warp_shape == 1)
         render_kernel<FMT, MODE, ERT, 16, PATH><<<grid, block, 0, st>>>(c, v, out, out_fmt, rl, rs);
     else if (MODE == kSearchAlg2 && warp_shape == 2)
         render_kernel<FMT, MODE, ERT, 8, PATH><<<grid, block, 0, st>>>(c, v, out, out_fmt, rl, rs);
     else
-        render_kernel<FMT, MODE, ERT, 32, PATH><<<grid, block, 0, st>>>(c, v, out, out_fmt, rl, rs);
+        render_kernel<FMT, MODE, ERT, 4, PATH><<<grid, block, 0, st>>>(c, v, out, out_fmt, rl, rs);
     return cudaGetLastError();
 }
 

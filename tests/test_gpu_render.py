@@ -133,7 +133,7 @@ def test_search_modes_and_warp_shapes_give_identical_images(V, ctx, search):
     try:
         cn = S.orbit_camera(case.bmin, case.bmax, 1.0, az_deg=30, el_deg=20)
         base = gpu_render(V, vdi, cn, 64, 64)
-        for ws in (0, 1, 2):
+        for ws in (0, 1, 2, 3):
             got = gpu_render(V, vdi, cn, 64, 64, search=search, warp_shape=ws)
             assert np.array_equal(got, base)
     finally:
