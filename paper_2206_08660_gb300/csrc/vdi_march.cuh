@@ -181,7 +181,7 @@ struct Seg {
 template <int FMT, int MODE, bool ERT, bool TOUCH>
 __device__ __forceinline__ bool process_list(const DevVdi &v, const Seg &g, int li, float s_in, float s_out,
                                              int &p, Accum &acc, uint32_t &n_lists, uint32_t &n_segs,
-                                             uint32_t *bm) {
+                                             uint32_t *bm, bool &hot) {
     const float d_in = fmaf(s_in, g.dz, g.z0), d_out = fmaf(s_out, g.dz, g.z0);
     ++n_lists;
     PairCache pc;
@@ -190,8 +190,11 @@ __device__ __forceinline__ bool process_list(const DevVdi &v, const Seg &g, int 
     cc.k = -1;
     {  // the ray crosses this list entirely before its first or after its last supersegment
         const float2 rg = __ldg(v.range + li);
-        if (MODE == kSearchAlg2 && p >= 0) {
+        if (MODE == kSearchAlg2 && p >= 0 && hot) {
             // the seed's depth and colour records, fetched together with the range
+            // while the ray is in a run of lists it meets (hot: the previous
+            // list passed its range test); a ray passing above or below the
+            // data skips that speculative fetch
             pc.k = p >> 1;
             pc.d = ld_depth_pair(v, pc.k, li);
             fetch_colour_pair<FMT>(cc, v, li, pc.k);
@@ -200,7 +203,8 @@ __device__ __forceinline__ bool process_list(const DevVdi &v, const Seg &g, int 
             mark_word<TOUCH>(bm, range_word_base(v) + 2 * (size_t)li);
             mark_word<TOUCH>(bm, range_word_base(v) + 2 * (size_t)li + 1);
         }
-        if (fmaxf(d_in, d_out) < rg.x || fminf(d_in, d_out) > rg.y) return false;
+        hot = !(fmaxf(d_in, d_out) < rg.x || fminf(d_in, d_out) > rg.y);
+        if (!hot) return false;
     }
     int last = -1, first;
     if (g.dz >= 0.f) {
@@ -296,6 +300,7 @@ __device__ __forceinline__ void march_exact(const DevVdi &v, Ray &r, Accum &acc,
     // Algorithm 2 with the front-most supersegment (the one it most likely
     // meets first); a ray whose depth decreases runs the plain binary search
     int p = (g.dz >= 0.f) ? 0 : -1;
+    bool hot = true;
     float s_in = 0.f;
     bool checked = !BLOCKS;
     const int maxit = v.w + v.h + 2 + (BLOCKS ? (v.bw + v.bh + 2) : 0);
@@ -338,7 +343,7 @@ __device__ __forceinline__ void march_exact(const DevVdi &v, Ray &r, Accum &acc,
         }
         const float s_out = fminf(fminf(sx, sy), 1.f);
         if (s_out > s_in) {
-            if (process_list<FMT, MODE, ERT, TOUCH>(v, g, iy * v.w + ix, s_in, s_out, p, acc, n_lists, n_segs, bm))
+            if (process_list<FMT, MODE, ERT, TOUCH>(v, g, iy * v.w + ix, s_in, s_out, p, acc, n_lists, n_segs, bm, hot))
                 break;
         }
         if (s_out >= 1.f) break;
@@ -394,6 +399,7 @@ __device__ __forceinline__ void march_exact_ess(const DevVdi &v, Ray &r, Accum &
     int ix = 0, iy = 0, bx = 0, by = 0;
     float sx = 0.f, sy = 0.f, s_l_in = 0.f;
     bool lvalid = false, in_cell = false, fresh = true;
+    bool hot = true;
     int p = -1;
     // One flat loop: every iteration is either one list step inside an occupied
     // cell or one cell step, so the lanes of a warp stay in step.
@@ -403,7 +409,7 @@ __device__ __forceinline__ void march_exact_ess(const DevVdi &v, Ray &r, Accum &
             const float s_l_out = fminf(sx, sy);
             const float a = fmaxf(s_l_in, sc_in), b = fminf(s_l_out, sc_out);
             if (b > a &&
-                process_list<FMT, MODE, ERT, TOUCH>(v, g, iy * v.w + ix, a, b, p, acc, n_lists, n_segs, bm))
+                process_list<FMT, MODE, ERT, TOUCH>(v, g, iy * v.w + ix, a, b, p, acc, n_lists, n_segs, bm, hot))
                 return;
             if (s_l_out >= sc_out) {  // the list continues beyond this cell
                 in_cell = false;
