@@ -70,7 +70,7 @@ def lib():
         L.orc_first_index.argtypes = [P, P, C.c_int, C.c_float, C.c_float, C.c_int]
         L.orc_first_index.restype = C.c_int
         L.orc_generate.argtypes = [P, P, C.c_int, P, P, C.c_int, C.c_int, C.c_int, C.c_double,
-                                   C.c_double, C.c_double, C.c_int, P, P, P, C.c_int]
+                                   C.c_double, C.c_double, C.c_int, C.c_int, P, P, P, P, C.c_int]
         L.orc_dvr.argtypes = [P, P, C.c_int, P, P, C.c_int, C.c_int, C.c_double, C.c_double,
                               C.c_int, P, P, C.c_int]
         _lib = L
@@ -209,18 +209,22 @@ class Volume:
         self.v = v
 
 
-def generate(volume, knots, view, proj, w, h, ns, tau, step, u, fp32=False, nthreads=None):
-    """VDI generation (Eq. 1, fixed gamma = tau).  Returns VdiArrays-like (rgba, depth, counts)."""
+def generate(volume, knots, view, proj, w, h, ns, tau, step, u, fp32=False, nthreads=None, adaptive=False,
+             with_tau=False):
+    """VDI generation (Eq. 1 with fixed gamma = tau, or with ``adaptive`` the
+    per-ray gamma of Algorithm 3).  Returns VdiArrays-like (rgba, depth,
+    counts), plus the gamma each list used with ``with_tau``."""
     nthreads = nthreads or os.cpu_count()
     knots = np.ascontiguousarray(knots, np.float32)
     rgba = np.zeros((h, w, ns, 4), np.float32)
     depth = np.zeros((h, w, ns, 2), np.float32)
     counts = np.zeros((h, w), np.int32)
+    taus = np.zeros((h, w), np.float32)
     rc = lib().orc_generate(C.byref(volume.v), _ptr(knots), len(knots), _ptr(_cmarr(view)), _ptr(_cmarr(proj)),
-                            w, h, ns, float(tau), float(step), float(u), 1 if fp32 else 0, _ptr(rgba),
-                            _ptr(depth), _ptr(counts), nthreads)
+                            w, h, ns, float(tau), float(step), float(u), 1 if fp32 else 0, 1 if adaptive else 0,
+                            _ptr(rgba), _ptr(depth), _ptr(counts), _ptr(taus), nthreads)
     assert rc == 0, "unsupported camera or transfer function"
-    return rgba, depth, counts
+    return (rgba, depth, counts, taus) if with_tau else (rgba, depth, counts)
 
 
 def dvr(volume, knots, view, proj, w, h, step, u, fp32=False, nthreads=None, with_flags=False):

@@ -1,7 +1,7 @@
 /*
  * vdi_oracle_gen.c -- oracle for VDI generation (Section 3, Eq. 1 with a
- * fixed sensitivity gamma = tau) and for direct volume rendering at the same
- * samples.  TEST INFRASTRUCTURE, NOT PRODUCT (see vdi_oracle.c).
+ * fixed sensitivity gamma = tau, or the ray-adaptive gamma of Algorithm 3)
+ * and for direct volume rendering at the same samples.  TEST INFRASTRUCTURE, NOT PRODUCT (see vdi_oracle.c).
  *
  * Readings where the paper is silent:
  *  - the V_O projection is an OpenGL perspective frustum; the pixel-centre
@@ -111,10 +111,12 @@ static void to_float(const gen_consts_d *d, gen_consts_f *f) {
     }
 }
 
-/* mode 0: FP64 arithmetic; mode 1: FP32 arithmetic (IEEE, no contraction) */
+/* mode 0: FP64 arithmetic; mode 1: FP32 arithmetic (IEEE, no contraction).
+ * adaptive != 0: each list picks its own gamma by Algorithm 3 (tau unused);
+ * tau_out (nullable) receives the gamma each list used. */
 ORC_EXPORT int orc_generate(const orc_volume *vol, const float *knots, int nk, const double *view, const double *proj,
-                            int w, int h, int ns, double tau, double step, double u, int mode, float *rgba,
-                            float *depth, int32_t *counts, int nthreads) {
+                            int w, int h, int ns, double tau, double step, double u, int mode, int adaptive,
+                            float *rgba, float *depth, int32_t *counts, float *tau_out, int nthreads) {
     gen_consts_d gd;
     gen_consts_f gf;
     if (gen_constants(vol, knots, nk, view, proj, tau, step, u, &gd)) return 1;
@@ -127,9 +129,20 @@ ORC_EXPORT int orc_generate(const orc_volume *vol, const float *knots, int nk, c
             rg[j * 4 + 0] = rg[j * 4 + 1] = rg[j * 4 + 2] = rg[j * 4 + 3] = 0.0f;
             dp[j * 2 + 0] = dp[j * 2 + 1] = INFINITY;
         }
-        int n = mode ? gen_list_f(vol, &gf, li % w, li / w, w, h, ns, rg, dp)
-                     : gen_list_d(vol, &gd, li % w, li / w, w, h, ns, rg, dp);
+        const int px = li % w, py = li / w;
+        int n;
+        double t_used = tau;
+        if (mode) {
+            const float t = adaptive ? adaptive_tau_f(vol, &gf, px, py, w, h, ns) : gf.tau;
+            n = gen_list_tau_f(vol, &gf, px, py, w, h, ns, t, rg, dp);
+            t_used = t;
+        } else {
+            const double t = adaptive ? adaptive_tau_d(vol, &gd, px, py, w, h, ns) : gd.tau;
+            n = gen_list_tau_d(vol, &gd, px, py, w, h, ns, t, rg, dp);
+            t_used = t;
+        }
         counts[li] = n;
+        if (tau_out) tau_out[li] = (float)t_used;
     }
     return 0;
 }

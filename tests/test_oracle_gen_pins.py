@@ -196,3 +196,115 @@ def test_near_plane_inside_the_box_clips_generation(orc):
         ch = chord(pn, pf, bmin, bmax)
         assert ch is not None and ch[0] == 0.0  # the ray starts on the near plane, inside the box
         assert counts[iy, ix] == 1 and abs(depth[iy, ix, 0, 0] - (-1.0)) < 1e-5
+
+
+# ---------------------------------------------------------------------------
+# Ray-adaptive sensitivity (Section 3, Algorithm 3 of the supplement)
+# ---------------------------------------------------------------------------
+GAMMA0 = np.float32(1e-5)
+
+
+def test_adaptive_gamma_on_a_constant_volume_keeps_the_start_value(orc):
+    """Every sample of a constant volume is identical, so gamma = 1e-5 already
+    gives one supersegment (< N_S): each ray keeps gamma = 1e-5 and the VDI is
+    the fixed-gamma one (the closed form of test_constant_volume_closed_form)."""
+    n = 16
+    vol = np.full((n, n, n), 0.45, np.float32)
+    bmin, bmax = np.zeros(3), np.ones(3)
+    cam = S.orbit_camera(bmin, bmax, 1.0, el_deg=20, az_deg=30)
+    kn = S.tf_knots("dense")
+    V = orc.Volume(vol, bmin, bmax)
+    for fp32 in (False, True):
+        rgba, depth, counts, taus = orc.generate(V, kn, cam.view, cam.proj, 12, 12, 4, 0.3, 1 / n, 1 / n, fp32=fp32,
+                                                 adaptive=True, with_tau=True)
+        fixed = orc.generate(V, kn, cam.view, cam.proj, 12, 12, 4, float(GAMMA0), 1 / n, 1 / n, fp32=fp32)
+        assert np.all(taus == GAMMA0)
+        assert counts.max() == 1 and counts.sum() > 50
+        for a, b in zip((rgba, depth, counts), fixed):
+            assert np.array_equal(a, b)
+
+
+def _band_check(orc, V, kn, cam, w, h, ns, u, rgba, depth, counts, taus):
+    """Classify every list's gamma with the writing path of fixed-gamma
+    generation at budget N_S + 1, which yields min(n(gamma), N_S + 1)."""
+    delta = (15 * ns) // 100
+    n_at = np.zeros((h, w), np.int64)
+    for t in np.unique(taus):
+        sel = taus == t
+        _, _, c = orc.generate(V, kn, cam.view, cam.proj, w, h, ns + 1, float(t), u, u, fp32=True)
+        n_at[sel] = c[sel]
+    first = taus == GAMMA0
+    band = (n_at >= ns - delta) & (n_at <= ns)
+    converged = ~first & ~band
+    # gamma = 1e-5 is kept only when it already gives at most N_S (fewer than
+    # N_S, or inside the band)
+    assert np.all(n_at[first] <= ns)
+    # the generated VDI is the fixed-gamma VDI of each list's gamma
+    assert np.all(counts <= ns)
+    assert np.all(counts[band] == n_at[band])
+    # lists that ended by the interval width took the upper end, a gamma that
+    # gave fewer than N_S - delta
+    assert np.all(n_at[converged] < ns - delta)
+    searched = ~first
+    return searched.mean(), band[searched].mean(), converged[searched].mean()
+
+
+@pytest.mark.parametrize("ns", [6, 12])
+def test_adaptive_gamma_lands_in_the_budget_band(orc, ns):
+    vol = S.value_noise_volume(32, octaves=4, seed=5, dtype=np.uint16)
+    bmin, bmax = S.bbox_for_dims(vol.shape)
+    cam = S.orbit_camera(bmin, bmax, 1.0, el_deg=15, az_deg=20)
+    V = orc.Volume(vol, bmin, bmax)
+    kn = S.tf_knots("dense")
+    u = 1 / 32
+    w = h = 20
+    rgba, depth, counts, taus = orc.generate(V, kn, cam.view, cam.proj, w, h, ns, 0.0, u, u, fp32=True,
+                                             adaptive=True, with_tau=True)
+    f_searched, f_band, f_conv = _band_check(orc, V, kn, cam, w, h, ns, u, rgba, depth, counts, taus)
+    # of the lists that had to search, most end inside the band
+    assert f_searched > 0.2 and f_band > 0.75 and f_conv < 0.25, (f_searched, f_band, f_conv)
+    # the budget is used: adaptive lists carry more supersegments than a coarse fixed gamma
+    assert counts[taus != GAMMA0].mean() >= ns - (15 * ns) // 100 - 1
+
+
+def test_adaptive_vdi_still_renders_to_dvr_at_the_original_view(orc):
+    """Check a' holds for any per-ray gamma: every supersegment stores the exact
+    composite of its samples."""
+    vol = S.blobs_volume(32, seed=4)
+    bmin, bmax = S.bbox_for_dims(vol.shape)
+    cam = S.orbit_camera(bmin, bmax, 1.0, el_deg=25, az_deg=40)
+    V = orc.Volume(vol, bmin, bmax)
+    kn = S.tf_knots("dense")
+    u = 1 / 32
+    for fp32 in (False, True):
+        rgba, depth, counts, taus = orc.generate(V, kn, cam.view, cam.proj, 32, 32, 5, 0.0, u, u, fp32=fp32,
+                                                 adaptive=True, with_tau=True)
+        assert counts.max() <= 5 and len(np.unique(taus)) > 10
+        sc = orc.Scene(S.VdiArrays(32, 32, 5, rgba, depth, counts), cam.view, cam.proj, bmin, bmax, u)
+        dvr = orc.dvr(V, kn, cam.view, cam.proj, 32, 32, u, u)
+        assert dvr[:, 3].max() > 0.5
+        assert np.abs(orc.render_direct(sc) - dvr).max() < 2e-6
+
+
+def test_eq1_threshold_is_the_l2_distance_of_premultiplied_colours(orc):
+    """Two constant slabs, red then blue, with the same opacity: the
+    premultiplied colours of their samples are a'(1, 0, 0) and a'(0, 0, 1),
+    L2 distance D = sqrt(2) a', and samples near the interface lie between
+    them.  A sensitivity above D merges everything into one supersegment per
+    ray; one well below D must split at the interface."""
+    n = 32
+    vol = np.zeros((n, n, n), np.float32)
+    vol[:, :, : n // 2] = 0.25
+    vol[:, :, n // 2:] = 0.75
+    bmin, bmax = np.zeros(3), np.ones(3)
+    a = 0.05
+    kn = np.array([[0.25, 1, 0, 0, a], [0.75, 0, 0, 1, a]], np.float32)
+    cam = S.orbit_camera(bmin, bmax, 1.0, el_deg=0.0, az_deg=90.0)  # looks along -x, across the interface
+    V = orc.Volume(vol, bmin, bmax)
+    D = np.sqrt(2.0) * a  # step = u: a' = a
+    _, _, c_hi = orc.generate(V, kn, cam.view, cam.proj, 9, 9, 8, 1.1 * D, 1 / n, 1 / n)
+    _, _, c_lo = orc.generate(V, kn, cam.view, cam.proj, 9, 9, 8, 0.4 * D, 1 / n, 1 / n)
+    hit = c_hi > 0
+    assert hit.sum() >= 25
+    assert np.all(c_hi[hit] == 1)
+    assert np.all(c_lo[hit] >= 2)
