@@ -441,6 +441,27 @@ def main():
                          wl["tau"], u, u, wl["fmt"])
     torch.cuda.synchronize()
     gen_s = time.perf_counter() - t
+
+    def timed_generate(**kw):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        g = V.vdi_generate(ctx, vol_d, bmin, bmax, kn, V.camera(cam_o.view, cam_o.proj), wl["w"], wl["h"],
+                           wl["ns"], wl["tau"], u, u, wl["fmt"], stream=stream, **kw)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1)
+        counts = V.vdi_download(g, wl["w"], wl["h"], wl["ns"])[2]
+        V.vdi_destroy(g)
+        hit = counts > 0
+        return ms, float(counts[hit].mean()) if hit.any() else 0.0
+
+    generation = {}
+    if rank == 0 and not args.no_serving:
+        gen_ms, seg_fixed = timed_generate()
+        ada_ms, seg_ada = timed_generate(adaptive=True)
+        generation = {"fixed_tau_ms": gen_ms, "adaptive_ms": ada_ms, "mean_supersegments_fixed": seg_fixed,
+                      "mean_supersegments_adaptive": seg_ada,
+                      "note": "one vdi_generate of the workload's VDI, CUDA events; adaptive = Algorithm 3"}
     del vol_d
     torch.cuda.empty_cache()
     layout = V.vdi_get_layout(vdi)
@@ -565,7 +586,7 @@ def main():
                      "algorithmic_bytes_per_launch": [int(b) for b in touched]},
         "clocks": clocks, "e2e": e2e, "gpu_launches": launches_per_step * args.steps, "ablation": ablation,
         "roofline_near_original_view": near,
-        "vdi_generate_ms": gen_s * 1e3, "vdi_bytes": int(layout.depth_bytes + layout.colour_bytes),
+        "vdi_generate_ms": gen_s * 1e3, "generation": generation, "vdi_bytes": int(layout.depth_bytes + layout.colour_bytes),
     }
     if not args.no_serving:
         srv = serving_leg(V, torch, ctx, dev)

@@ -343,6 +343,11 @@ typedef struct {
     double length_unit;  /* world length the stored and transfer-function alphas refer to */
     int colour_fmt;      /* VDI_F32 or VDI_F16 */
     int grid_tile, grid_nz; /* count grid (0 -> 8, 20) */
+    int adaptive;        /* 0: gamma = tau for every ray; 1: each ray finds its own gamma by the
+                            bisection of Section 3 (Algorithm 3 of the supplement): in [0, sqrt(3)],
+                            from 1e-5, until it gets N_S - floor(0.15 N_S) .. N_S supersegments or
+                            the interval is narrower than 1e-4; tau is then ignored */
+    float *tau_out;      /* DEVICE [h][w] or NULL: the gamma each list used */
 } vdi_gen_params;
 
 vdi_status vdi_generate(vdi_ctx *ctx, const vdi_volume *vol, const vdi_tf *tf, const vdi_gen_params *params,

@@ -70,7 +70,7 @@ class VdiTf(C.Structure):
 class VdiGenParams(C.Structure):
     _fields_ = [("w", C.c_int), ("h", C.c_int), ("n_s", C.c_int), ("orig", VdiCamera), ("tau", C.c_float),
                 ("step", C.c_double), ("length_unit", C.c_double), ("colour_fmt", C.c_int),
-                ("grid_tile", C.c_int), ("grid_nz", C.c_int)]
+                ("grid_tile", C.c_int), ("grid_nz", C.c_int), ("adaptive", C.c_int), ("tau_out", C.c_void_p)]
 
 
 class VdiRequest(C.Structure):
@@ -303,8 +303,10 @@ _VOL_DTYPE = {"uint8": 0, "uint16": 1, "float32": 2}
 
 
 def vdi_generate(ctx, volume, bbox_min, bbox_max, knots, cam_o: VdiCamera, w, h, n_s, tau, step, length_unit,
-                 colour_fmt=VDI_F32, grid_tile=0, grid_nz=0, stream=None):
-    """volume: torch CUDA tensor [nz, ny, nx] of uint8/uint16/float32; knots: (n, 5) array."""
+                 colour_fmt=VDI_F32, grid_tile=0, grid_nz=0, stream=None, adaptive=False, tau_out=None):
+    """volume: torch CUDA tensor [nz, ny, nx] of uint8/uint16/float32; knots: (n, 5) array.
+    adaptive: per-ray gamma (Algorithm 3) instead of tau; tau_out: optional float32 CUDA
+    tensor [h, w] that receives each list's gamma."""
     vol = VdiVolume()
     vol.nz, vol.ny, vol.nx = (int(x) for x in volume.shape)
     vol.dtype = _VOL_DTYPE[str(volume.dtype).replace("torch.", "")]
@@ -318,6 +320,10 @@ def vdi_generate(ctx, volume, bbox_min, bbox_max, knots, cam_o: VdiCamera, w, h,
     p.w, p.h, p.n_s, p.orig = int(w), int(h), int(n_s), cam_o
     p.tau, p.step, p.length_unit = float(tau), float(step), float(length_unit)
     p.colour_fmt, p.grid_tile, p.grid_nz = int(colour_fmt), int(grid_tile), int(grid_nz)
+    p.adaptive = 1 if adaptive else 0
+    if tau_out is not None:
+        assert str(tau_out.dtype) == "torch.float32" and tau_out.numel() >= int(w) * int(h)
+        p.tau_out = _dptr(tau_out)
     out = P()
     _check(load().vdi_generate(ctx, C.byref(vol), C.byref(tf), C.byref(p), _stream(stream), C.byref(out)))
     return out

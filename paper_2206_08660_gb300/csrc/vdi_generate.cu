@@ -1,5 +1,6 @@
 // vdi_generate.cu -- VDI generation from a scalar volume (Section 3, Eq. 1
-// with a fixed sensitivity gamma = tau), one thread per V_O pixel ray.
+// with a fixed sensitivity gamma = tau or the ray-adaptive gamma of
+// Algorithm 3), one thread per V_O pixel ray.
 //
 // Arithmetic uses explicit round-to-nearest FP32 intrinsics with no fused
 // multiply-add, in a fixed order, so the integer outcome of generation (how
@@ -34,6 +35,7 @@ struct GenConsts {
     int nx, ny, nz, dtype;
     const void *data;
     int fmt;
+    int adaptive;  // 1: per-ray gamma by Algorithm 3 (tau unused)
 };
 
 #define ADD __fadd_rn
@@ -90,7 +92,6 @@ __device__ __forceinline__ void classify(const GenConsts &g, float v, float out[
 }
 
 struct SegWriter {
-    int nseg;
     float pf, pb;      // pending even slot (depth)
     float4 pc;         // pending even slot (colour)
 };
@@ -117,44 +118,27 @@ __device__ __forceinline__ void write_pair(const GenConsts &g, float4 *depth, vo
     }
 }
 
-__global__ void __launch_bounds__(256) generate_kernel(const GenConsts g, float4 *__restrict__ depth,
-                                                       void *__restrict__ colour, float2 *__restrict__ range) {
-    const int px = blockIdx.x * 32 + (threadIdx.x & 31);
-    const int py = blockIdx.y * 8 + (threadIdx.x >> 5);
-    if (px >= g.w || py >= g.h) return;
-    const long long li = (long long)py * g.w + px;
-    SegWriter sw;
-    sw.nseg = 0;
-    sw.pf = sw.pb = INFINITY;
-    sw.pc = make_float4(0.f, 0.f, 0.f, 0.f);
+// The V_O pixel-centre ray of list (px, py), clipped to near/far and the box;
+// K samples of view-depth step dt from t0.
+struct GenRay {
+    float dir[3];
+    float len, t0, dt;
+    long long K;
+};
 
-    float first_f = INFINITY, last_b = -INFINITY;
-    auto emit = [&](float f, float b, float4 col) {
-        if (sw.nseg == 0) first_f = f;
-        last_b = b;
-        const int j = sw.nseg++;
-        if ((j & 1) == 0) {
-            sw.pf = f;
-            sw.pb = b;
-            sw.pc = col;
-        } else {
-            write_pair(g, depth, colour, li, j >> 1, sw.pf, sw.pb, sw.pc, f, b, col);
-        }
-    };
-
-    // ---- ray through the pixel centre, clipped to V_O near/far and the box
+__device__ __forceinline__ GenRay gen_ray(const GenConsts &g, int px, int py) {
+    GenRay r;
     const float x = SUB(DIV(MUL(2.f, ADD((float)px, 0.5f)), (float)g.w), 1.f);
     const float y = SUB(1.f, DIV(MUL(2.f, ADD((float)py, 0.5f)), (float)g.h));
-    float dir[3];
 #pragma unroll
-    for (int c = 0; c < 3; ++c) dir[c] = ADD(ADD(g.D0[c], MUL(x, g.Dx[c])), MUL(y, g.Dy[c]));
-    const float len = __fsqrt_rn(ADD(ADD(MUL(dir[0], dir[0]), MUL(dir[1], dir[1])), MUL(dir[2], dir[2])));
+    for (int c = 0; c < 3; ++c) r.dir[c] = ADD(ADD(g.D0[c], MUL(x, g.Dx[c])), MUL(y, g.Dy[c]));
+    r.len = __fsqrt_rn(ADD(ADD(MUL(r.dir[0], r.dir[0]), MUL(r.dir[1], r.dir[1])), MUL(r.dir[2], r.dir[2])));
     float t0 = g.t_near, t1 = g.t_far;
     bool hit = true;
 #pragma unroll
     for (int c = 0; c < 3; ++c) {
-        if (dir[c] != 0.f) {
-            float ta = DIV(SUB(g.bmin[c], g.E[c]), dir[c]), tb = DIV(SUB(g.bmax[c], g.E[c]), dir[c]);
+        if (r.dir[c] != 0.f) {
+            float ta = DIV(SUB(g.bmin[c], g.E[c]), r.dir[c]), tb = DIV(SUB(g.bmax[c], g.E[c]), r.dir[c]);
             if (ta > tb) {
                 const float s = ta;
                 ta = tb;
@@ -166,51 +150,84 @@ __global__ void __launch_bounds__(256) generate_kernel(const GenConsts g, float4
             hit = false;
         }
     }
-    long long K = 0;
-    float dt = 0.f;
+    r.K = 0;
+    r.t0 = t0;
+    r.dt = 0.f;
     if (hit && t0 < t1) {
-        const float L = MUL(SUB(t1, t0), len);
+        const float L = MUL(SUB(t1, t0), r.len);
         const float kq = floorf(DIV(L, g.step));
-        K = kq < (float)kMaxSamples ? (long long)kq : kMaxSamples;
-        dt = DIV(g.step, len);
+        r.K = kq < (float)kMaxSamples ? (long long)kq : kMaxSamples;
+        r.dt = DIV(g.step, r.len);
     }
+    return r;
+}
 
-    // ---- march, segment (Eq. 1), composite
+// One march along the ray with sensitivity tau (Eq. 1).  WRITE: supersegments
+// go to the VDI, the N_S-th never closes, returns how many were written.
+// !WRITE (the counting pass of Algorithm 3): no limit on the number, nothing
+// written, and the count stops at ns + 1 ("more than N_S").
+template <bool WRITE>
+__device__ int gen_march(const GenConsts &g, const GenRay &r, float tau, float4 *__restrict__ depth,
+                         void *__restrict__ colour, long long li, float &first_f, float &last_b) {
+    const int limit = WRITE ? g.ns : g.ns + 2;  // supersegment number `limit` never closes
+    int nseg = 0;
+    SegWriter sw;
+    sw.pf = sw.pb = INFINITY;
+    sw.pc = make_float4(0.f, 0.f, 0.f, 0.f);
     bool open = false;
     float t_start = 0.f, t_end = 0.f, Tseg = 1.f, Tray = 1.f;
     float mean[3] = {0.f, 0.f, 0.f}, Cacc[3] = {0.f, 0.f, 0.f};
     int cnt = 0;
-    const float tau2 = MUL(g.tau, g.tau);
+    const float tau2 = MUL(tau, tau);
     auto close = [&]() {
-        const float f = SUB(DIV(g.P23, t_start), g.P22);
-        const float b = SUB(DIV(g.P23, t_end), g.P22);
-        const float aacc = 1.f - Tseg;
-        const float Lu = (t_end - t_start) * len / g.u;  // world length in length units
-        const float ia = aacc > 0.f ? 1.f / aacc : 0.f;
-        float kappa = (Lu > 0.f) ? -log2f(Tseg) / Lu : 0.f;
-        emit(f, b, make_float4(fminf(Cacc[0] * ia, 1.f), fminf(Cacc[1] * ia, 1.f), fminf(Cacc[2] * ia, 1.f), kappa));
+        if (WRITE) {
+            const float f = SUB(DIV(g.P23, t_start), g.P22);
+            const float b = SUB(DIV(g.P23, t_end), g.P22);
+            const float aacc = 1.f - Tseg;
+            const float Lu = (t_end - t_start) * r.len / g.u;  // world length in length units
+            const float ia = aacc > 0.f ? 1.f / aacc : 0.f;
+            const float kappa = (Lu > 0.f) ? -log2f(Tseg) / Lu : 0.f;
+            const float4 col =
+                make_float4(fminf(Cacc[0] * ia, 1.f), fminf(Cacc[1] * ia, 1.f), fminf(Cacc[2] * ia, 1.f), kappa);
+            if (nseg == 0) first_f = f;
+            last_b = b;
+            if ((nseg & 1) == 0) {
+                sw.pf = f;
+                sw.pb = b;
+                sw.pc = col;
+            } else {
+                write_pair(g, depth, colour, li, nseg >> 1, sw.pf, sw.pb, sw.pc, f, b, col);
+            }
+        }
+        ++nseg;
         open = false;
     };
-    for (long long k = 0; k < K; ++k) {
+    for (long long k = 0; k < r.K; ++k) {
         const float fk = (float)k;
-        const float ta = ADD(t0, MUL(fk, dt));
-        const float tm = ADD(t0, MUL(ADD(fk, 0.5f), dt));
-        const float tb = ADD(t0, MUL((float)(k + 1), dt));
+        const float ta = ADD(r.t0, MUL(fk, r.dt));
+        const float tm = ADD(r.t0, MUL(ADD(fk, 0.5f), r.dt));
+        const float tb = ADD(r.t0, MUL((float)(k + 1), r.dt));
         float p[3];
 #pragma unroll
-        for (int c = 0; c < 3; ++c) p[c] = ADD(g.E[c], MUL(tm, dir[c]));
+        for (int c = 0; c < 3; ++c) p[c] = ADD(g.E[c], MUL(tm, r.dir[c]));
         float tf[4];
         classify(g, trilinear(g, p), tf);
         const float a = g.step_is_u ? tf[3] : 1.f - powf(1.f - tf[3], g.adj_exp);
         if (!(a > 0.f)) {
-            if (open && sw.nseg < g.ns - 1) close();
+            if (open && nseg < limit - 1) {
+                close();
+                if (!WRITE && nseg > g.ns) return g.ns + 1;
+            }
             continue;
         }
         const float xc[3] = {MUL(tf[0], a), MUL(tf[1], a), MUL(tf[2], a)};
-        if (open && sw.nseg < g.ns - 1) {
+        if (open && nseg < limit - 1) {
             const float d0 = SUB(mean[0], xc[0]), d1 = SUB(mean[1], xc[1]), d2 = SUB(mean[2], xc[2]);
             const float dist2 = ADD(ADD(MUL(d0, d0), MUL(d1, d1)), MUL(d2, d2));
-            if (!(tau2 > dist2)) close();
+            if (!(tau2 > dist2)) {
+                close();
+                if (!WRITE && nseg > g.ns) return g.ns + 1;
+            }
         }
         if (!open) {
             open = true;
@@ -232,17 +249,68 @@ __global__ void __launch_bounds__(256) generate_kernel(const GenConsts g, float4
         if (Tray <= kErtT) break;
     }
     if (open) close();
-
-    // ---- pad the remaining slots
+    if (!WRITE) return nseg > g.ns ? g.ns + 1 : nseg;
+    // pad the remaining slots
     const float4 zero = make_float4(0.f, 0.f, 0.f, 0.f);
-    int j = sw.nseg;
+    int j = nseg;
     if (j & 1) {
         write_pair(g, depth, colour, li, j >> 1, sw.pf, sw.pb, sw.pc, INFINITY, INFINITY, zero);
         ++j;
     }
     for (; j < g.nsp; j += 2)
         write_pair(g, depth, colour, li, j >> 1, INFINITY, INFINITY, zero, INFINITY, INFINITY, zero);
+    return nseg;
+}
+
+// Ray-adaptive sensitivity (Section 3, Algorithm 3 of the supplement): a
+// bisection for gamma in [0, sqrt(3)] (the largest L2 distance of two
+// premultiplied RGB colours) until the ray gets between N_S - delta and N_S
+// supersegments, delta = floor(0.15 N_S).  The search starts at 1e-5 and
+// keeps it if that gives fewer than N_S; more than N_S raises the lower end,
+// fewer than N_S - delta lowers the upper end; an interval narrower than
+// 1e-4 ends the search with the upper end (the side that does not exceed
+// N_S).  FP32 with explicit rounding, like the march, so every ray's gamma is
+// reproducible.
+__device__ float adaptive_tau(const GenConsts &g, const GenRay &r) {
+    const int delta = (15 * g.ns) / 100;
+    float low = 0.f, high = (float)1.7320508075688772, gamma = (float)1e-5;
+    const float eps = (float)1e-4;
+    bool first = true, found = false;
+    float ff = 0.f, lb = 0.f;
+    while (!found) {
+        const int n = gen_march<false>(g, r, gamma, nullptr, nullptr, 0, ff, lb);
+        if (SUB(high, low) < eps) {
+            found = true;
+            gamma = high;
+        } else if (n > g.ns) {
+            low = gamma;
+        } else if (n < g.ns - delta) {
+            high = gamma;
+        } else {
+            found = true;
+        }
+        if (first) {
+            first = false;
+            if (n < g.ns) found = true;
+        }
+        if (!found) gamma = DIV(ADD(low, high), 2.f);
+    }
+    return gamma;
+}
+
+__global__ void __launch_bounds__(256) generate_kernel(const GenConsts g, float4 *__restrict__ depth,
+                                                       void *__restrict__ colour, float2 *__restrict__ range,
+                                                       float *__restrict__ tau_out) {
+    const int px = blockIdx.x * 32 + (threadIdx.x & 31);
+    const int py = blockIdx.y * 8 + (threadIdx.x >> 5);
+    if (px >= g.w || py >= g.h) return;
+    const long long li = (long long)py * g.w + px;
+    const GenRay r = gen_ray(g, px, py);
+    const float tau = g.adaptive ? adaptive_tau(g, r) : g.tau;
+    float first_f = INFINITY, last_b = -INFINITY;
+    gen_march<true>(g, r, tau, depth, colour, li, first_f, last_b);
     range[li] = make_float2(first_f, last_b);
+    if (tau_out) tau_out[li] = tau;
 }
 
 #undef ADD
@@ -346,9 +414,11 @@ VDI_API vdi_status vdi_generate(vdi_ctx *ctx, const vdi_volume *vol, const vdi_t
     g.dtype = vol->dtype;
     g.data = vol->data;
     g.fmt = d.colour_fmt;
+    g.adaptive = prm->adaptive ? 1 : 0;
     cudaStream_t st = (cudaStream_t)stream;
     dim3 grid(div_up(d.w, 32), div_up(d.h, 8));
-    generate_kernel<<<grid, 256, 0, st>>>(g, reinterpret_cast<float4 *>(v->depth_mem), v->colour_mem, v->range_mem);
+    generate_kernel<<<grid, 256, 0, st>>>(g, reinterpret_cast<float4 *>(v->depth_mem), v->colour_mem, v->range_mem,
+                                          prm->tau_out);
     cudaError_t e = cudaGetLastError();
     if (e == cudaSuccess) e = launch_grid(v->dv, v->grid_mem, st);
     if (e == cudaSuccess) e = launch_block_range(v->dv, v->brange_mem, st);
