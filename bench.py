@@ -374,6 +374,7 @@ def main():
     ap.add_argument("--workload", default="large", choices=list(WORKLOADS))
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-serving", action="store_true")
+    ap.add_argument("--no-quality", action="store_true", help="skip the DVR / SSIM quality study")
     ap.add_argument("--frames", default=None,
                     help="override the step's frames, e.g. '0:1:1,10:1:1' (degrees:D_I:D_R); for profiling")
     ap.add_argument("--cpu-budget", type=float, default=15.0, help="seconds of oracle work for cpu_baseline")
@@ -462,8 +463,6 @@ def main():
         generation = {"fixed_tau_ms": gen_ms, "adaptive_ms": ada_ms, "mean_supersegments_fixed": seg_fixed,
                       "mean_supersegments_adaptive": seg_ada,
                       "note": "one vdi_generate of the workload's VDI, CUDA events; adaptive = Algorithm 3"}
-    del vol_d
-    torch.cuda.empty_cache()
     layout = V.vdi_get_layout(vdi)
     cams = [V.camera(c.view, c.proj) for c in views]
     W, H = wl["W"], wl["H"]
@@ -572,6 +571,31 @@ def main():
            "h2d_bytes_per_step": cam_bytes * frames_per_step,
            "d2h_bytes_per_step": int(sum(o.numel() * o.element_size() for o in outs))}
 
+    # ---- quality study (Section 6, Fig. 9): each frame against GPU DVR from the same view
+    quality = {}
+    if rank == 0 and not args.no_quality:
+        ref = torch.empty((H, W, 4), dtype=torch.float32, device=dev)
+        img = torch.empty((H, W, 4), dtype=torch.float32, device=dev)
+        rows, dvr_ms = [], []
+        q_frames = [(0.0, 1, 1)] + list(wl["frames"])
+        for (az, d_i, d_r) in q_frames:
+            cn = S.orbit_camera(bmin, bmax, W / H, az_deg=az, el_deg=wl["el"], zoom=wl["zoom"])
+            cq = V.camera(cn.view, cn.proj)
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            V.vdi_dvr(ctx, vol_d, bmin, bmax, kn, cq, W, H, u, u, ref, V.VDI_F32, stream)
+            e1.record(stream)
+            V.vdi_render(vdi, cq, W, H, d_i, d_r, img, V.VDI_F32, stream)
+            torch.cuda.synchronize()
+            dvr_ms.append(e0.elapsed_time(e1))
+            s_v, p_v = V.vdi_image_quality(img, ref, V.VDI_F32, stream)
+            rows.append({"frame": f"{az:g}deg_di{d_i}_dr{d_r}", "ssim_vs_dvr": s_v, "psnr_vs_dvr": p_v})
+        quality = {"frames": rows, "dvr_ms_mean": float(np.mean(dvr_ms)),
+                   "note": "SSIM / PSNR over RGB (7x7 windows, data range 1) of each VDI frame against GPU DVR "
+                           "of the volume from the same view at a 1-voxel step (vdi_dvr, vdi_image_quality)"}
+    del vol_d
+    torch.cuda.empty_cache()
+
     launches_per_step = sum(1 if d_i == 1 else 2 for (_, d_i, _) in wl["frames"])
     result = {
         "metric": METRIC, "value": fps, "unit": "frames/s", "n_gpus": world, "steps": args.steps,
@@ -586,7 +610,7 @@ def main():
                      "algorithmic_bytes_per_launch": [int(b) for b in touched]},
         "clocks": clocks, "e2e": e2e, "gpu_launches": launches_per_step * args.steps, "ablation": ablation,
         "roofline_near_original_view": near,
-        "vdi_generate_ms": gen_s * 1e3, "generation": generation, "vdi_bytes": int(layout.depth_bytes + layout.colour_bytes),
+        "vdi_generate_ms": gen_s * 1e3, "generation": generation, "quality": quality, "vdi_bytes": int(layout.depth_bytes + layout.colour_bytes),
     }
     if not args.no_serving:
         srv = serving_leg(V, torch, ctx, dev)

@@ -353,6 +353,30 @@ typedef struct {
 vdi_status vdi_generate(vdi_ctx *ctx, const vdi_volume *vol, const vdi_tf *tf, const vdi_gen_params *params,
                         void *stream, vdi_t **out);
 
+/* ---- ground truth and image quality (Section 6) ----------------------------
+ * vdi_dvr: direct volume rendering of the volume from `view` (an OpenGL
+ * perspective frustum; the ray of pixel (px, py) runs through its centre from
+ * the near to the far plane, clipped to the box), with the sampling rules of
+ * vdi_generate: samples at the midpoints of world intervals of `step` from the
+ * box entry, trilinear interpolation, the transfer function, opacity
+ * 1 - (1 - alpha)^(step / length_unit), front-to-back emission-absorption
+ * compositing, early termination at transmittance 2^-12.  out_rgba: DEVICE
+ * W x H premultiplied RGBA of out_fmt (row 0 on top), caller-owned.
+ * Stream-ordered; argument errors are returned synchronously.
+ *
+ * vdi_image_quality: SSIM and PSNR of image `a` against reference `b`, the
+ * measures of the paper's evaluation (SSIM of Wang et al. 2004).  a, b: DEVICE
+ * W x H RGBA images of fmt (W, H >= 7); both measures use the R, G, B channels
+ * with data range 1.  SSIM: 7 x 7 windows fully inside the image, window
+ * means, sample variances and covariance (divided by 48), C1 = 0.01^2,
+ * C2 = 0.03^2, mean over windows and channels.  PSNR = 10 log10(1 / MSE) over
+ * all pixels and channels (+inf for identical images).  Results are written to
+ * the host doubles; the call synchronises `stream`. */
+vdi_status vdi_dvr(vdi_ctx *ctx, const vdi_volume *vol, const vdi_tf *tf, const vdi_camera *view, int W, int H,
+                   double step, double length_unit, void *out_rgba, int out_fmt, void *stream);
+vdi_status vdi_image_quality(const void *a, const void *b, int W, int H, int fmt, double *ssim, double *psnr,
+                             void *stream);
+
 /* ---- render without device allocation -------------------------------------
  * The paper has no counterpart to this entry point.  It renders exactly what
  * vdi_render renders, but the low-resolution image of an image-space preview

@@ -143,6 +143,8 @@ def load(build_if_needed: bool = True):
     _sig(L, "vdi_render_ex", [P, P, C.c_int, C.c_int, C.c_int, C.c_int, P, C.c_int, P, P])
     _sig(L, "vdi_search_first", [P, C.c_int, C.c_int, P, P, P, P, P, C.c_int, P])
     _sig(L, "vdi_generate", [P, P, P, P, P, C.POINTER(P)])
+    _sig(L, "vdi_dvr", [P, P, P, P, C.c_int, C.c_int, C.c_double, C.c_double, P, C.c_int, P])
+    _sig(L, "vdi_image_quality", [P, P, C.c_int, C.c_int, C.c_int, C.POINTER(C.c_double), C.POINTER(C.c_double), P])
     _sig(L, "vdi_touch_bitmap", [P, P, C.c_int, C.c_int, P, C.c_size_t, P])
     _sig(L, "vdi_render_batch", [P, P, C.c_int, P, P])
     _sig(L, "vdi_autotune_batch", [P, P, C.c_int, P, P, P])
@@ -327,6 +329,38 @@ def vdi_generate(ctx, volume, bbox_min, bbox_max, knots, cam_o: VdiCamera, w, h,
     out = P()
     _check(load().vdi_generate(ctx, C.byref(vol), C.byref(tf), C.byref(p), _stream(stream), C.byref(out)))
     return out
+
+
+def _volume_tf(volume, bbox_min, bbox_max, knots):
+    vol = VdiVolume()
+    vol.nz, vol.ny, vol.nx = (int(x) for x in volume.shape)
+    vol.dtype = _VOL_DTYPE[str(volume.dtype).replace("torch.", "")]
+    vol.data = _dptr(volume)
+    vol.bbox_min = (C.c_double * 3)(*map(float, bbox_min))
+    vol.bbox_max = (C.c_double * 3)(*map(float, bbox_max))
+    kn = np.ascontiguousarray(knots, np.float32)
+    tf = VdiTf()
+    tf.n_knots, tf.knots = len(kn), kn.ctypes.data
+    return vol, tf, kn
+
+
+def vdi_dvr(ctx, volume, bbox_min, bbox_max, knots, view: VdiCamera, W, H, step, length_unit, out,
+            out_fmt=VDI_F32, stream=None):
+    """Direct volume rendering (ground truth) into ``out`` (CUDA tensor [H, W, 4] of out_fmt)."""
+    vol, tf, kn = _volume_tf(volume, bbox_min, bbox_max, knots)
+    _check(load().vdi_dvr(ctx, C.byref(vol), C.byref(tf), C.byref(view), int(W), int(H), float(step),
+                          float(length_unit), _dptr(out), int(out_fmt), _stream(stream)))
+    del kn
+
+
+def vdi_image_quality(a, b, fmt=VDI_F32, stream=None):
+    """(SSIM, PSNR) of image ``a`` against reference ``b`` (CUDA tensors [H, W, 4] of fmt)."""
+    H, W = int(a.shape[0]), int(a.shape[1])
+    assert tuple(b.shape[:2]) == (H, W)
+    ssim, psnr = C.c_double(), C.c_double()
+    _check(load().vdi_image_quality(_dptr(a), _dptr(b), W, H, int(fmt), C.byref(ssim), C.byref(psnr),
+                                    _stream(stream)))
+    return ssim.value, psnr.value
 
 
 def vdi_touch_bitmap(vdi, cam: VdiCamera, W, H, bitmap, stream=None):

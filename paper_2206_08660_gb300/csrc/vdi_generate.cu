@@ -313,6 +313,50 @@ __global__ void __launch_bounds__(256) generate_kernel(const GenConsts g, float4
     if (tau_out) tau_out[li] = tau;
 }
 
+// Direct volume rendering (emission-absorption, front to back) of the volume
+// from any perspective camera, at the generation's sampling rules: midpoints
+// of world intervals of `step` from the box entry, trilinear interpolation,
+// the transfer function, a' = 1 - (1 - alpha)^(step / u), early termination
+// at transmittance 2^-12.  It is the ground truth the VDI renders are compared
+// with (Section 6).  One thread per pixel; output premultiplied RGBA.
+__global__ void __launch_bounds__(256) dvr_kernel(const GenConsts g, void *__restrict__ out, int out_fmt) {
+    const int px = blockIdx.x * 32 + (threadIdx.x & 31);
+    const int py = blockIdx.y * 8 + (threadIdx.x >> 5);
+    if (px >= g.w || py >= g.h) return;
+    const GenRay r = gen_ray(g, px, py);
+    float C[3] = {0.f, 0.f, 0.f}, T = 1.f;
+    for (long long k = 0; k < r.K; ++k) {
+        const float tm = ADD(r.t0, MUL(ADD((float)k, 0.5f), r.dt));
+        float p[3];
+#pragma unroll
+        for (int c = 0; c < 3; ++c) p[c] = ADD(g.E[c], MUL(tm, r.dir[c]));
+        float tf[4];
+        classify(g, trilinear(g, p), tf);
+        const float a = g.step_is_u ? tf[3] : 1.f - powf(1.f - tf[3], g.adj_exp);
+        if (!(a > 0.f)) continue;
+        const float wgt = MUL(T, a);
+#pragma unroll
+        for (int c = 0; c < 3; ++c) C[c] = ADD(C[c], MUL(wgt, tf[c]));
+        T = MUL(T, SUB(1.f, a));
+        if (T <= kErtT) break;
+    }
+    const size_t idx = (size_t)py * g.w + px;
+    if (out_fmt == 0) {
+        reinterpret_cast<float4 *>(out)[idx] = make_float4(C[0], C[1], C[2], 1.f - T);
+    } else {
+        uint2 q;
+        q.x = h2bits(C[0], C[1]);
+        q.y = h2bits(C[2], 1.f - T);
+        reinterpret_cast<uint2 *>(out)[idx] = q;
+    }
+}
+
+cudaError_t launch_dvr(const GenConsts &g, void *out, int out_fmt, cudaStream_t st) {
+    dim3 grid(div_up(g.w, 32), div_up(g.h, 8));
+    dvr_kernel<<<grid, 256, 0, st>>>(g, out, out_fmt);
+    return cudaGetLastError();
+}
+
 #undef ADD
 #undef SUB
 #undef MUL
@@ -328,10 +372,10 @@ using namespace vdi;
 
 static double pe(const double *m, int r, int c) { return m[c * 4 + r]; }
 
-VDI_API vdi_status vdi_generate(vdi_ctx *ctx, const vdi_volume *vol, const vdi_tf *tf, const vdi_gen_params *prm,
-                                void *stream, vdi_t **out) {
-    if (!ctx || !vol || !tf || !prm || !out) return fail(VDI_ERR_INVALID_ARG, "NULL argument");
-    *out = nullptr;
+// Validation shared by generation and DVR: the volume, the transfer function,
+// the sampling step and a perspective camera (the rays are parameterised by
+// its view depth).
+static vdi_status check_volume_tf_camera(const vdi_volume *vol, const vdi_tf *tf, const vdi_camera *cam, double step) {
     if (!vol->data || vol->nx < 1 || vol->ny < 1 || vol->nz < 1 || vol->dtype < 0 || vol->dtype > 2)
         return fail(VDI_ERR_INVALID_ARG, "bad volume");
     if (tf->n_knots < 2 || tf->n_knots > 16 || !tf->knots) return fail(VDI_ERR_INVALID_ARG, "n_knots in 2..16");
@@ -344,18 +388,67 @@ VDI_API vdi_status vdi_generate(vdi_ctx *ctx, const vdi_volume *vol, const vdi_t
         for (int c = 1; c < 4; ++c)
             if (kn[c] < 0.f || kn[c] > 1.f) return fail(VDI_ERR_INVALID_ARG, "knot colour outside [0,1]");
     }
-    if (!(prm->step > 0.0) || !(prm->tau >= 0.f) || !isfinite(prm->tau))
-        return fail(VDI_ERR_INVALID_ARG, "step must be > 0 and tau >= 0");
-    {
-        double diag = 0.0;
-        for (int k = 0; k < 3; ++k) diag += (vol->bbox_max[k] - vol->bbox_min[k]) * (vol->bbox_max[k] - vol->bbox_min[k]);
-        if (!(sqrt(diag) / prm->step < (double)kMaxSamples))
-            return fail(VDI_ERR_INVALID_ARG, "step too small: more than %lld samples per ray", kMaxSamples);
-    }
-    const double *P = prm->orig.proj;
+    if (!(step > 0.0)) return fail(VDI_ERR_INVALID_ARG, "step must be > 0");
+    double diag = 0.0;
+    for (int k = 0; k < 3; ++k) diag += (vol->bbox_max[k] - vol->bbox_min[k]) * (vol->bbox_max[k] - vol->bbox_min[k]);
+    if (!(sqrt(diag) / step < (double)kMaxSamples))
+        return fail(VDI_ERR_INVALID_ARG, "step too small: more than %lld samples per ray", kMaxSamples);
+    const double *P = cam->proj;
     if (!(pe(P, 3, 0) == 0 && pe(P, 3, 1) == 0 && pe(P, 3, 2) == -1 && pe(P, 3, 3) == 0 && pe(P, 2, 0) == 0 &&
           pe(P, 2, 1) == 0 && pe(P, 0, 1) == 0 && pe(P, 1, 0) == 0 && pe(P, 0, 3) == 0 && pe(P, 1, 3) == 0))
-        return fail(VDI_ERR_UNSUPPORTED, "generation needs an OpenGL perspective frustum for V_O");
+        return fail(VDI_ERR_UNSUPPORTED, "generation and DVR need an OpenGL perspective frustum");
+    return VDI_OK;
+}
+
+// Per-camera ray constants (host FP64, rounded to FP32 once).
+static vdi_status make_gen_consts(const vdi_volume *vol, const vdi_tf *tf, const vdi_camera *cam, int w, int h,
+                                  double step, double length_unit, GenConsts *g) {
+    const double *P = cam->proj;
+    double Vi[16];
+    if (!mat4_inv(cam->view, Vi)) return fail(VDI_ERR_INVALID_ARG, "camera view is singular");
+    *g = GenConsts{};
+    const double dv0[3] = {pe(P, 0, 2) / pe(P, 0, 0), pe(P, 1, 2) / pe(P, 1, 1), -1.0};
+    for (int r = 0; r < 3; ++r) {
+        g->E[r] = (float)(pe(Vi, r, 3) / pe(Vi, 3, 3));
+        double s0 = 0.0;
+        for (int c = 0; c < 3; ++c) s0 += pe(Vi, r, c) * dv0[c];
+        g->D0[r] = (float)s0;
+        g->Dx[r] = (float)(pe(Vi, r, 0) * (1.0 / pe(P, 0, 0)));
+        g->Dy[r] = (float)(pe(Vi, r, 1) * (1.0 / pe(P, 1, 1)));
+        g->bmin[r] = (float)vol->bbox_min[r];
+        g->bmax[r] = (float)vol->bbox_max[r];
+        g->ext[r] = g->bmax[r] - g->bmin[r];  // one IEEE float subtraction (host code is built without contraction)
+    }
+    g->P22 = (float)pe(P, 2, 2);
+    g->P23 = (float)pe(P, 2, 3);
+    g->t_near = (float)(pe(P, 2, 3) / (pe(P, 2, 2) - 1.0));
+    g->t_far = (float)(pe(P, 2, 3) / (pe(P, 2, 2) + 1.0));
+    g->step = (float)step;
+    g->u = (float)length_unit;
+    g->step_is_u = g->step == g->u;
+    g->adj_exp = g->step / g->u;
+    g->nk = tf->n_knots;
+    for (int k = 0; k < g->nk; ++k) {
+        g->kv[k] = tf->knots[5 * k];
+        for (int c = 0; c < 4; ++c) g->kc[k][c] = tf->knots[5 * k + 1 + c];
+    }
+    g->w = w;
+    g->h = h;
+    g->nx = vol->nx;
+    g->ny = vol->ny;
+    g->nz = vol->nz;
+    g->dtype = vol->dtype;
+    g->data = vol->data;
+    return VDI_OK;
+}
+
+VDI_API vdi_status vdi_generate(vdi_ctx *ctx, const vdi_volume *vol, const vdi_tf *tf, const vdi_gen_params *prm,
+                                void *stream, vdi_t **out) {
+    if (!ctx || !vol || !tf || !prm || !out) return fail(VDI_ERR_INVALID_ARG, "NULL argument");
+    *out = nullptr;
+    vdi_status st_ = check_volume_tf_camera(vol, tf, &prm->orig, prm->step);
+    if (st_ != VDI_OK) return st_;
+    if (!(prm->tau >= 0.f) || !isfinite(prm->tau)) return fail(VDI_ERR_INVALID_ARG, "tau must be >= 0");
     vdi_desc d{};
     d.w = prm->w;
     d.h = prm->h;
@@ -369,50 +462,17 @@ VDI_API vdi_status vdi_generate(vdi_ctx *ctx, const vdi_volume *vol, const vdi_t
     d.colour_fmt = prm->colour_fmt;
     d.grid_tile = prm->grid_tile;
     d.grid_nz = prm->grid_nz;
-    double Vi[16];
-    if (!mat4_inv(prm->orig.view, Vi)) return fail(VDI_ERR_INVALID_ARG, "V_O view is singular");
+    GenConsts g;
+    st_ = make_gen_consts(vol, tf, &prm->orig, d.w, d.h, prm->step, prm->length_unit, &g);
+    if (st_ != VDI_OK) return st_;
     cudaSetDevice(ctx->device);
     vdi_t *v = nullptr;
-    vdi_status st_ = alloc_vdi(ctx, &d, (cudaStream_t)stream, &v);
+    st_ = alloc_vdi(ctx, &d, (cudaStream_t)stream, &v);
     if (st_ != VDI_OK) return st_;
-
-    GenConsts g{};
-    const double dv0[3] = {pe(P, 0, 2) / pe(P, 0, 0), pe(P, 1, 2) / pe(P, 1, 1), -1.0};
-    for (int r = 0; r < 3; ++r) {
-        g.E[r] = (float)(pe(Vi, r, 3) / pe(Vi, 3, 3));
-        double s0 = 0.0;
-        for (int c = 0; c < 3; ++c) s0 += pe(Vi, r, c) * dv0[c];
-        g.D0[r] = (float)s0;
-        g.Dx[r] = (float)(pe(Vi, r, 0) * (1.0 / pe(P, 0, 0)));
-        g.Dy[r] = (float)(pe(Vi, r, 1) * (1.0 / pe(P, 1, 1)));
-        g.bmin[r] = (float)vol->bbox_min[r];
-        g.bmax[r] = (float)vol->bbox_max[r];
-        g.ext[r] = g.bmax[r] - g.bmin[r];  // one IEEE float subtraction (host code is built without contraction)
-    }
-    g.P22 = (float)pe(P, 2, 2);
-    g.P23 = (float)pe(P, 2, 3);
-    g.t_near = (float)(pe(P, 2, 3) / (pe(P, 2, 2) - 1.0));
-    g.t_far = (float)(pe(P, 2, 3) / (pe(P, 2, 2) + 1.0));
-    g.step = (float)prm->step;
-    g.u = (float)prm->length_unit;
     g.tau = prm->tau;
-    g.step_is_u = g.step == g.u;
-    g.adj_exp = g.step / g.u;
-    g.nk = tf->n_knots;
-    for (int k = 0; k < g.nk; ++k) {
-        g.kv[k] = tf->knots[5 * k];
-        for (int c = 0; c < 4; ++c) g.kc[k][c] = tf->knots[5 * k + 1 + c];
-    }
-    g.w = d.w;
-    g.h = d.h;
     g.ns = d.n_s;
     g.nsp = v->dv.nsp;
     g.nl = v->dv.nl;
-    g.nx = vol->nx;
-    g.ny = vol->ny;
-    g.nz = vol->nz;
-    g.dtype = vol->dtype;
-    g.data = vol->data;
     g.fmt = d.colour_fmt;
     g.adaptive = prm->adaptive ? 1 : 0;
     cudaStream_t st = (cudaStream_t)stream;
@@ -429,4 +489,20 @@ VDI_API vdi_status vdi_generate(vdi_ctx *ctx, const vdi_volume *vol, const vdi_t
     }
     *out = v;
     return VDI_OK;
+}
+
+VDI_API vdi_status vdi_dvr(vdi_ctx *ctx, const vdi_volume *vol, const vdi_tf *tf, const vdi_camera *view, int W, int H,
+                           double step, double length_unit, void *out_rgba, int out_fmt, void *stream) {
+    if (!ctx || !vol || !tf || !view || !out_rgba) return fail(VDI_ERR_INVALID_ARG, "NULL argument");
+    if (W < 1 || H < 1 || (long long)W * H > (1LL << 30)) return fail(VDI_ERR_INVALID_ARG, "image %dx%d", W, H);
+    if (out_fmt != VDI_F32 && out_fmt != VDI_F16) return fail(VDI_ERR_INVALID_ARG, "out_fmt=%d", out_fmt);
+    if (!(length_unit > 0.0)) return fail(VDI_ERR_INVALID_ARG, "length_unit must be > 0");
+    vdi_status st_ = check_volume_tf_camera(vol, tf, view, step);
+    if (st_ != VDI_OK) return st_;
+    GenConsts g;
+    st_ = make_gen_consts(vol, tf, view, W, H, step, length_unit, &g);
+    if (st_ != VDI_OK) return st_;
+    cudaSetDevice(ctx->device);
+    cudaError_t e = launch_dvr(g, out_rgba, out_fmt, (cudaStream_t)stream);
+    return e == cudaSuccess ? VDI_OK : cuda_fail(e, "dvr");
 }
