@@ -365,6 +365,44 @@ def serving_leg(V, torch, ctx, dev, cfg=SERVING):
                           "requests": len(sat)}}
 
 
+def preview_control_leg(V, torch, vdi, wl, bmin, bmax, stream, frames=240, target_ms=0.3, d_r=1):
+    """The preview-rate PI controller (Section 4.4) in a session: the view orbits
+    0 -> 45 -> 0 degrees over `frames` frames at the display resolution; each
+    frame is rendered at the scale the controller chose from the previous
+    frame's measured time (vdi_render_scaled), D_R fixed.  Every 20th frame is
+    scored (SSIM) against the full-resolution exact render of the same view."""
+    W, H = wl["W"], wl["H"]
+    pi = V.PiController(target_ms, W, H)
+    out = torch.empty((H, W, 4), dtype=torch.float16, device="cuda")
+    full = torch.empty((H, W, 4), dtype=torch.float16, device="cuda")
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    times, scales, ssims = [], [], []
+    s, Wr, Hr = pi.current()
+    for k in range(frames):
+        az = 45.0 * (1.0 - abs(1.0 - 2.0 * k / (frames - 1)))
+        cn = S.orbit_camera(bmin, bmax, W / H, az_deg=az, el_deg=wl["el"], zoom=wl["zoom"])
+        cam = V.camera(cn.view, cn.proj)
+        e0.record(stream)
+        V.vdi_render_scaled(vdi, cam, W, H, Wr, Hr, d_r, out, V.VDI_F16, stream)
+        e1.record(stream)
+        e1.synchronize()
+        ms = e0.elapsed_time(e1)
+        times.append(ms)
+        scales.append(s)
+        if k % 20 == 10:
+            V.vdi_render(vdi, cam, W, H, 1, 1, full, V.VDI_F16, stream)
+            ssims.append(V.vdi_image_quality(out, full, V.VDI_F16, stream)[0])
+        s, Wr, Hr = pi.update(ms)
+    t = np.array(times[20:])
+    return {"target_ms": target_ms, "frames": frames, "d_r": d_r, "path": "orbit 0 -> 45 -> 0 deg",
+            "frame_ms_mean": float(t.mean()), "frame_ms_p95": float(np.percentile(t, 95)),
+            "within_20pct": float(np.mean(np.abs(t - target_ms) <= 0.2 * target_ms)),
+            "scale_mean": float(np.mean(scales)), "scale_min": float(np.min(scales)),
+            "ssim_vs_full_mean": float(np.mean(ssims)), "ssim_vs_full_min": float(np.min(ssims)),
+            "note": "CUDA-event frame times with a sync per frame (the controller needs each measurement); "
+                    "statistics exclude the first 20 frames"}
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -595,6 +633,11 @@ def main():
                            "of the volume from the same view at a 1-voxel step (vdi_dvr, vdi_image_quality)"}
     del vol_d
     torch.cuda.empty_cache()
+    control = {}
+    if rank == 0 and not args.no_quality:
+        control = {"dr1_target0.5ms": preview_control_leg(V, torch, vdi, wl, bmin, bmax, stream, target_ms=0.5, d_r=1),
+                   "dr2_target0.25ms": preview_control_leg(V, torch, vdi, wl, bmin, bmax, stream, target_ms=0.25,
+                                                           d_r=2)}
 
     launches_per_step = sum(1 if d_i == 1 else 2 for (_, d_i, _) in wl["frames"])
     result = {
@@ -610,7 +653,7 @@ def main():
                      "algorithmic_bytes_per_launch": [int(b) for b in touched]},
         "clocks": clocks, "e2e": e2e, "gpu_launches": launches_per_step * args.steps, "ablation": ablation,
         "roofline_near_original_view": near,
-        "vdi_generate_ms": gen_s * 1e3, "generation": generation, "quality": quality, "vdi_bytes": int(layout.depth_bytes + layout.colour_bytes),
+        "vdi_generate_ms": gen_s * 1e3, "generation": generation, "quality": quality, "preview_control": control, "vdi_bytes": int(layout.depth_bytes + layout.colour_bytes),
     }
     if not args.no_serving:
         srv = serving_leg(V, torch, ctx, dev)

@@ -194,6 +194,40 @@ vdi_status vdi_render(vdi_t *vdi, const vdi_camera *view, int W, int H, int d_i,
 vdi_status vdi_render_ex(vdi_t *vdi, const vdi_camera *view, int W, int H, int d_i, int d_r,
                          void *out_rgba, int out_fmt, const vdi_render_opts *opts, void *stream);
 
+/* vdi_render with any image-space scale (the paper's fractional D_I, Section
+ * 4.4): Wr x Hr rays (1 <= Wr <= W, 1 <= Hr <= H) over the same image plane,
+ * bilinearly upsampled to the W x H output (half-pixel centres, clamp to
+ * edge); Wr = ceil(W / d_i), Hr = ceil(H / d_i) gives exactly vdi_render's
+ * d_i preview.  The low-resolution image comes from the stream-ordered
+ * allocator.  Errors as vdi_render. */
+vdi_status vdi_render_scaled(vdi_t *vdi, const vdi_camera *view, int W, int H, int Wr, int Hr, int d_r,
+                             void *out_rgba, int out_fmt, void *stream);
+
+/* ---- preview-rate controller (Section 4.4) ---------------------------------
+ * A proportional-integral controller that picks the image-space scale s (the
+ * paper's D_I: fraction of the display resolution rendered per axis) so that
+ * frames keep a target frame time; the caller keeps D_R.  The paper names the
+ * controller type only; the law here runs on logarithms (frame time grows
+ * about with s^2): e = ln(target / measured), I += ki e (skipped while s sits
+ * at a bound and e pushes it further out), ln s = clamp(ln scale_start + kp e
+ * + I, ln scale_min, ln scale_max).  The next frame is rendered at
+ * round(s W) x round(s H) rays, halves rounding up (vdi_render_scaled).  Host-only
+ * state; no GPU work.  vdi_pi_update takes the measured time of the frame
+ * rendered at the current scale and returns the scale and ray counts of the
+ * next one. */
+typedef struct {
+    double target_ms;                 /* target frame time (> 0) */
+    double kp, ki;                    /* gains (>= 0); 0.1 and 0.3 are the defaults of the binding */
+    double scale_min, scale_max;      /* 0 < scale_min <= scale_max <= 1 */
+    double scale_start;               /* first frame's scale, inside the bounds */
+    int W, H;                         /* display resolution */
+} vdi_pi_config;
+typedef struct vdi_pi vdi_pi;
+vdi_status vdi_pi_create(const vdi_pi_config *cfg, vdi_pi **out);
+vdi_status vdi_pi_current(const vdi_pi *pi, double *scale, int *Wr, int *Hr);
+vdi_status vdi_pi_update(vdi_pi *pi, double frame_ms, double *scale, int *Wr, int *Hr);
+void vdi_pi_destroy(vdi_pi *pi);
+
 /* ---- batched multi-view rendering ---------------------------------------
  * Render up to VDI_BATCH_MAX_REQUESTS views of up to VDI_BATCH_MAX_VDIS
  * resident VDIs (of any resolutions, formats, previews) in one persistent

@@ -144,6 +144,11 @@ def load(build_if_needed: bool = True):
     _sig(L, "vdi_search_first", [P, C.c_int, C.c_int, P, P, P, P, P, C.c_int, P])
     _sig(L, "vdi_generate", [P, P, P, P, P, C.POINTER(P)])
     _sig(L, "vdi_dvr", [P, P, P, P, C.c_int, C.c_int, C.c_double, C.c_double, P, C.c_int, P])
+    _sig(L, "vdi_render_scaled", [P, P, C.c_int, C.c_int, C.c_int, C.c_int, C.c_int, P, C.c_int, P])
+    _sig(L, "vdi_pi_create", [P, C.POINTER(P)])
+    _sig(L, "vdi_pi_current", [P, C.POINTER(C.c_double), C.POINTER(C.c_int), C.POINTER(C.c_int)])
+    _sig(L, "vdi_pi_update", [P, C.c_double, C.POINTER(C.c_double), C.POINTER(C.c_int), C.POINTER(C.c_int)])
+    _sig(L, "vdi_pi_destroy", [P], None)
     _sig(L, "vdi_image_quality", [P, P, C.c_int, C.c_int, C.c_int, C.POINTER(C.c_double), C.POINTER(C.c_double), P])
     _sig(L, "vdi_touch_bitmap", [P, P, C.c_int, C.c_int, P, C.c_size_t, P])
     _sig(L, "vdi_render_batch", [P, P, C.c_int, P, P])
@@ -361,6 +366,43 @@ def vdi_image_quality(a, b, fmt=VDI_F32, stream=None):
     _check(load().vdi_image_quality(_dptr(a), _dptr(b), W, H, int(fmt), C.byref(ssim), C.byref(psnr),
                                     _stream(stream)))
     return ssim.value, psnr.value
+
+
+def vdi_render_scaled(vdi, view: VdiCamera, W, H, Wr, Hr, d_r, out, out_fmt=VDI_F32, stream=None):
+    """Render Wr x Hr rays and upsample bilinearly into ``out`` (CUDA tensor [H, W, 4])."""
+    _check(load().vdi_render_scaled(vdi, C.byref(view), int(W), int(H), int(Wr), int(Hr), int(d_r), _dptr(out),
+                                    int(out_fmt), _stream(stream)))
+
+
+class VdiPiConfig(C.Structure):
+    _fields_ = [("target_ms", C.c_double), ("kp", C.c_double), ("ki", C.c_double), ("scale_min", C.c_double),
+                ("scale_max", C.c_double), ("scale_start", C.c_double), ("W", C.c_int), ("H", C.c_int)]
+
+
+class PiController:
+    """The preview-rate PI controller (vdi_pi_*): ``update(frame_ms)`` returns
+    (scale, Wr, Hr) for the next frame."""
+
+    def __init__(self, target_ms, W, H, kp=0.1, ki=0.3, scale_min=0.1, scale_max=1.0, scale_start=1.0):
+        cfg = VdiPiConfig(float(target_ms), float(kp), float(ki), float(scale_min), float(scale_max),
+                          float(scale_start), int(W), int(H))
+        self._p = P()
+        _check(load().vdi_pi_create(C.byref(cfg), C.byref(self._p)))
+
+    def current(self):
+        s, w, h = C.c_double(), C.c_int(), C.c_int()
+        _check(load().vdi_pi_current(self._p, C.byref(s), C.byref(w), C.byref(h)))
+        return s.value, w.value, h.value
+
+    def update(self, frame_ms):
+        s, w, h = C.c_double(), C.c_int(), C.c_int()
+        _check(load().vdi_pi_update(self._p, float(frame_ms), C.byref(s), C.byref(w), C.byref(h)))
+        return s.value, w.value, h.value
+
+    def __del__(self):
+        if getattr(self, "_p", None):
+            load().vdi_pi_destroy(self._p)
+            self._p = None
 
 
 def vdi_touch_bitmap(vdi, cam: VdiCamera, W, H, bitmap, stream=None):

@@ -597,6 +597,30 @@ done:
     return st_;
 }
 
+VDI_API vdi_status vdi_render_scaled(vdi_t *v, const vdi_camera *view, int W, int H, int Wr, int Hr, int d_r,
+                                     void *out_rgba, int out_fmt, void *stream) {
+    vdi_status st_ = check_render_args(v, W, H, 1, d_r, out_rgba, out_fmt);
+    if (st_ != VDI_OK) return st_;
+    if (Wr < 1 || Hr < 1 || Wr > W || Hr > H) return fail(VDI_ERR_INVALID_ARG, "rays %dx%d for image %dx%d", Wr, Hr, W, H);
+    cudaSetDevice(v->ctx->device);
+    cudaStream_t st = (cudaStream_t)stream;
+    ViewConsts c;
+    st_ = make_view_consts(v, view, Wr, Hr, d_r, &c);
+    if (st_ != VDI_OK) return st_;
+    const int ws = default_warp_shape(v, Wr, Hr);
+    float4 *lo = nullptr;
+    if (Wr == W && Hr == H) {
+        CK(launch_render(c, v->dv, out_rgba, out_fmt, nullptr, nullptr, VDI_SEARCH_ALG2, ws, true, false, false, st));
+    } else {
+        CK(cudaMallocAsync((void **)&lo, (size_t)Wr * Hr * sizeof(float4), st));
+        CK(launch_render(c, v->dv, lo, VDI_F32, nullptr, nullptr, VDI_SEARCH_ALG2, ws, true, false, false, st));
+        CK(launch_upsample(lo, Wr, Hr, out_rgba, out_fmt, W, H, st));
+    }
+done:
+    if (lo) cudaFreeAsync(lo, st);
+    return st_;
+}
+
 VDI_API vdi_status vdi_render(vdi_t *v, const vdi_camera *view, int W, int H, int d_i, int d_r, void *out_rgba,
                               int out_fmt, void *stream) {
     return vdi_render_ex(v, view, W, H, d_i, d_r, out_rgba, out_fmt, nullptr, stream);

@@ -83,3 +83,37 @@ def test_image_space_preview(V, orc, scene, d_i, d_r):
     got = render(V, vdi[0], cn, W, H, d_i, d_r)
     assert (~touched).mean() > 0.6
     check_tolerance(got, ref, 0, mask=~touched, what=f"D_I={d_i} D_R={d_r}")
+
+
+@pytest.mark.parametrize("Wr,Hr,d_r", [(45, 31, 1), (37, 61, 1), (90, 61, 1), (52, 35, 2)])
+def test_fractional_image_scale(V, orc, scene, Wr, Hr, d_r):
+    """vdi_render_scaled: any ray count per axis (the paper's fractional D_I),
+    upsampled to the display; against the oracle's render at Wr x Hr and its
+    bilinear upsampling."""
+    case, sc, vdi = scene
+    W, H = 90, 61
+    cn = S.orbit_camera(case.bmin, case.bmax, W / H, az_deg=30, el_deg=20)
+    if d_r == 1:
+        lo = orc.render_exact(sc, cn.view, cn.proj, Wr, Hr)[0]
+        fl = np.zeros(Wr * Hr)
+    else:
+        lo, fl = orc.render_preview(sc, cn.view, cn.proj, Wr, Hr, d_r, T, NZ)
+    ref = orc.upsample(lo, Wr, Hr, W, H)
+    touched = orc.upsample(np.repeat(fl.astype(np.float64)[:, None], 4, 1), Wr, Hr, W, H)[:, 0] > 0
+    out = torch.zeros((H, W, 4), dtype=torch.float32, device="cuda")
+    V.vdi_render_scaled(vdi[0], V.camera(cn.view, cn.proj), W, H, Wr, Hr, d_r, out)
+    torch.cuda.synchronize()
+    assert (~touched).mean() > 0.6
+    check_tolerance(out.cpu().numpy().reshape(-1, 4), ref, 0, mask=~touched, what=f"{Wr}x{Hr} D_R={d_r}")
+
+
+def test_scaled_render_equals_integer_preview(V, scene):
+    case, sc, vdi = scene
+    W, H = 90, 61
+    cn = S.orbit_camera(case.bmin, case.bmax, W / H, az_deg=-20, el_deg=10)
+    for d_i in (1, 2, 3):
+        a = render(V, vdi[1], cn, W, H, d_i, 1)
+        out = torch.zeros((H, W, 4), dtype=torch.float32, device="cuda")
+        V.vdi_render_scaled(vdi[1], V.camera(cn.view, cn.proj), W, H, -(-W // d_i), -(-H // d_i), 1, out)
+        torch.cuda.synchronize()
+        assert np.array_equal(out.cpu().numpy().reshape(-1, 4), a)
