@@ -281,6 +281,42 @@ vdi_status make_view_consts(const vdi_t *v, const vdi_camera *cam, int W, int H,
     c->inv_u = (float)(1.0 / v->desc.length_unit);
     c->W = W;
     c->H = H;
+    // The pixel rectangle around the image of the box's eight corners under
+    // V_N (their convex hull holds every pixel centre whose ray meets the
+    // box), widened by a pixel; the whole image when a corner is not in front
+    // of the camera.
+    c->rx0 = 0;
+    c->rx1 = W - 1;
+    c->ry0 = 0;
+    c->ry1 = H - 1;
+    {
+        double PV[16];
+        mat4_mul(cam->proj, cam->view, PV);
+        double xlo = INFINITY, xhi = -INFINITY, ylo = INFINITY, yhi = -INFINITY;
+        bool front = true;
+        for (int corner = 0; corner < 8 && front; ++corner) {
+            const double p[4] = {(corner & 1) ? v->desc.bbox_max[0] : v->desc.bbox_min[0],
+                                 (corner & 2) ? v->desc.bbox_max[1] : v->desc.bbox_min[1],
+                                 (corner & 4) ? v->desc.bbox_max[2] : v->desc.bbox_min[2], 1.0};
+            double q[4];
+            mat4_apply(PV, p, q);
+            if (!(q[3] > 1e-12)) {
+                front = false;
+                break;
+            }
+            const double px = (q[0] / q[3] + 1.0) * 0.5 * W - 0.5, py = (1.0 - q[1] / q[3]) * 0.5 * H - 0.5;
+            xlo = fmin(xlo, px);
+            xhi = fmax(xhi, px);
+            ylo = fmin(ylo, py);
+            yhi = fmax(yhi, py);
+        }
+        if (front && isfinite(xlo) && isfinite(xhi) && isfinite(ylo) && isfinite(yhi)) {
+            c->rx0 = (int)fmax(floor(xlo) - 1.0, -1.0);
+            c->rx1 = (int)fmin(ceil(xhi) + 1.0, (double)W);
+            c->ry0 = (int)fmax(floor(ylo) - 1.0, -1.0);
+            c->ry1 = (int)fmin(ceil(yhi) + 1.0, (double)H);
+        }
+    }
     c->sx = (float)(2.0 / W);
     c->sy = (float)(2.0 / H);
     c->d_r = d_r;

@@ -70,6 +70,7 @@ struct ViewConsts {
     float bmin[3], bmax[3];
     float inv_u;        // 1 / length_unit
     int W, H;           // rays rendered (after D_I)
+    int rx0, rx1, ry0, ry1;  // pixel rectangle holding the box's image; rays outside it miss the box
     float sx, sy;       // 2/W, 2/H
     int d_r;            // ray subsampling (1 = exact path)
     float cell_scale;   // length_unit / (slab view-depth extent * d_r)

@@ -43,6 +43,7 @@ __device__ __forceinline__ void clip_lin(float c0, float c1, float &t0, float &t
 constexpr float kPreciseSlope = 64.f;  // lists per ray below which list crossings need an FP64 start
 
 __device__ __forceinline__ bool setup_ray(const ViewConsts &c, int px, int py, int vw, int vh, Ray &r) {
+    if (px < c.rx0 || px > c.rx1 || py < c.ry0 || py > c.ry1) return false;  // outside the box's image
     const float fpx = (float)px, fpy = (float)py;
     // pixel centre in V_N NDC (FP32 is enough for the world-space box clip)
     const float x = fmaf(fpx + 0.5f, c.sx, -1.f), y = fmaf(-(fpy + 0.5f), c.sy, 1.f);
@@ -178,10 +179,11 @@ struct Seg {
 // Algorithm 2 (seeded with p, the last index met in the previous list),
 // adjacency walk, Eq. 2 per piece, front-to-back compositing.  Returns true
 // once the ray is opaque (early termination).
-template <int FMT, int MODE, bool ERT, bool TOUCH>
+// PRE: the caller has already loaded the list's range (rg_pre).
+template <int FMT, int MODE, bool ERT, bool TOUCH, bool PRE = false>
 __device__ __forceinline__ bool process_list(const DevVdi &v, const Seg &g, int li, float s_in, float s_out,
                                              int &p, Accum &acc, uint32_t &n_lists, uint32_t &n_segs,
-                                             uint32_t *bm, bool &hot) {
+                                             uint32_t *bm, bool &hot, float2 rg_pre = make_float2(0.f, 0.f)) {
     const float d_in = fmaf(s_in, g.dz, g.z0), d_out = fmaf(s_out, g.dz, g.z0);
     ++n_lists;
     PairCache pc;
@@ -189,7 +191,7 @@ __device__ __forceinline__ bool process_list(const DevVdi &v, const Seg &g, int 
     ColourCache<FMT> cc;
     cc.k = -1;
     {  // the ray crosses this list entirely before its first or after its last supersegment
-        const float2 rg = __ldg(v.range + li);
+        const float2 rg = PRE ? rg_pre : __ldg(v.range + li);
         if (MODE == kSearchAlg2 && p >= 0 && hot) {
             // the seed's depth and colour records, fetched together with the range
             // while the ray is in a run of lists it meets (hot: the previous
@@ -304,6 +306,40 @@ __device__ __forceinline__ void march_exact(const DevVdi &v, Ray &r, Accum &acc,
     float s_in = 0.f;
     bool checked = !BLOCKS;
     const int maxit = v.w + v.h + 2 + (BLOCKS ? (v.bw + v.bh + 2) : 0);
+    if (!BLOCKS) {
+        // the walk with the next list's range requested one list ahead, so its
+        // load overlaps the work on the current list
+        int li = iy * v.w + ix;
+        float2 rg = __ldg(v.range + li);
+        for (int it = 0; it < maxit; ++it) {
+            const float s_out = fminf(fminf(sx, sy), 1.f);
+            const bool xs = sx <= sy;
+            const int nix = xs ? ix + stx : ix, niy = xs ? iy : iy + sty;
+            const bool nin = (unsigned)nix < (unsigned)v.w && (unsigned)niy < (unsigned)v.h;
+            const int nli = nin ? niy * v.w + nix : li;
+            float2 rg_next = rg;
+            if (nin && s_out < 1.f) rg_next = __ldg(v.range + nli);  // not when the ray ends in this list
+            if (s_out > s_in) {
+                if (process_list<FMT, MODE, ERT, TOUCH, true>(v, g, li, s_in, s_out, p, acc, n_lists, n_segs, bm,
+                                                              hot, rg))
+                    break;
+            }
+            if (s_out >= 1.f || !nin) break;
+            if (xs) {
+                fbx += fsx;
+                sx = fmaf(fbx, idgx, cx0);
+            } else {
+                fby += fsy;
+                sy = fmaf(fby, idgy, cy0);
+            }
+            ix = nix;
+            iy = niy;
+            li = nli;
+            rg = rg_next;
+            s_in = fmaxf(s_in, s_out);
+        }
+        return;
+    }
     for (int it = 0; it < maxit; ++it) {
         if (BLOCKS && !checked) {
             const int cbx = ix / kB, cby = iy / kB;
