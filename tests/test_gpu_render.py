@@ -264,3 +264,37 @@ def test_range_block_skipping_is_bit_identical(V, ctx, fmt):
                 assert np.array_equal(a, b), (seed, az)
         finally:
             V.vdi_destroy(vdi)
+
+
+@pytest.mark.parametrize("w,h,ns", [(1, 1, 1), (3, 40, 1), (40, 3, 2), (17, 11, 64), (9, 7, 63)])
+def test_extreme_list_counts_and_grid_shapes(V, ctx, orc, w, h, ns):
+    """One list, one-list-wide grids, N_S = 1 and the largest N_S (64, and an
+    odd 63 that leaves a padding slot), rendered from several views."""
+    case = random_case(w, h, ns, seed=w * 100 + ns, u=0.2, alpha_range=(0.05, 0.6), fill=1.0)
+    sc = case.oracle_scene(orc)
+    vdi = V.vdi_create(ctx, case.gpu_desc(V, 0), case.vdi.rgba, case.vdi.depth, case.vdi.counts)
+    try:
+        shown = 0.0
+        for (az, el, zoom, ortho) in VIEWS:
+            W, H = 41, 33
+            cn = S.orbit_camera(case.bmin, case.bmax, W / H, az_deg=az, el_deg=el, zoom=zoom, ortho=ortho)
+            ref, _, _, fl = orc.render_exact(sc, cn.view, cn.proj, W, H)
+            got = gpu_render(V, vdi, cn, W, H)
+            shown = max(shown, float(ref[:, 3].max()))
+            check_tolerance(got, ref, 0, mask=fl == 0, what=f"{w}x{h} N_S={ns} view {az},{el}")
+        assert shown > 0.05
+    finally:
+        V.vdi_destroy(vdi)
+
+
+@pytest.mark.parametrize("W,H", [(1, 1), (1, 77), (77, 1), (33, 9)])
+def test_tiny_and_thin_images(V, ctx, orc, W, H):
+    case = random_case(24, 16, 4, seed=5, u=0.2)
+    sc = case.oracle_scene(orc)
+    vdi = V.vdi_create(ctx, case.gpu_desc(V, 1), case.vdi.rgba, case.vdi.depth, case.vdi.counts)
+    try:
+        cn = S.orbit_camera(case.bmin, case.bmax, W / H, az_deg=20.0, el_deg=10.0)
+        ref, _, _, fl = orc.render_exact(sc, cn.view, cn.proj, W, H)
+        check_tolerance(gpu_render(V, vdi, cn, W, H), ref, 1, mask=fl == 0, what=f"{W}x{H}")
+    finally:
+        V.vdi_destroy(vdi)
