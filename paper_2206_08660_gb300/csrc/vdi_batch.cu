@@ -60,8 +60,11 @@ struct UpParams {
     UpReq reqs[kMaxBatchReq];
 };
 
-template <int WX>
-__global__ void __launch_bounds__(256) batch_render_kernel(const BatchParams P) {
+// PREVIEW: the batch holds ray-subsampled previews (d_r > 1); without them the
+// kernel carries only the exact walk, which needs fewer registers, so more
+// blocks fit on an SM.
+template <int WX, bool PREVIEW>
+__global__ void __launch_bounds__(256, PREVIEW ? 3 : 4) batch_render_kernel(const BatchParams P) {
     __shared__ int s_tile, s_req;
     for (;;) {
         if (threadIdx.x == 0) {
@@ -96,7 +99,7 @@ __global__ void __launch_bounds__(256) batch_render_kernel(const BatchParams P) 
             uint32_t nl = 0, nsg = 0;
             Ray ray;
             if (setup_ray(q.c, px, py, v.w, v.h, ray)) {
-                if (q.c.d_r > 1) {
+                if (PREVIEW && q.c.d_r > 1) {
                     if (v.fmt == 0)
                         march_preview<0, kSearchAlg2, true>(v, q.c, ray, acc);
                     else
@@ -149,11 +152,16 @@ __global__ void __launch_bounds__(256) batch_upsample_kernel(const UpParams P) {
     store_px(q.out, q.out_fmt, (size_t)Y * q.W + X, acc);
 }
 
-static const void *render_fn(int ws) {
-    if (ws == 0) return (const void *)batch_render_kernel<32>;
-    if (ws == 1) return (const void *)batch_render_kernel<16>;
-    if (ws == 2) return (const void *)batch_render_kernel<8>;
-    return (const void *)batch_render_kernel<4>;
+template <bool PREVIEW>
+static const void *render_fn_p(int ws) {
+    if (ws == 0) return (const void *)batch_render_kernel<32, PREVIEW>;
+    if (ws == 1) return (const void *)batch_render_kernel<16, PREVIEW>;
+    if (ws == 2) return (const void *)batch_render_kernel<8, PREVIEW>;
+    return (const void *)batch_render_kernel<4, PREVIEW>;
+}
+
+static const void *render_fn(int ws, bool preview) {
+    return preview ? render_fn_p<true>(ws) : render_fn_p<false>(ws);
 }
 
 // ---------------------------------------------------------------------------
@@ -166,6 +174,7 @@ struct BatchPlan {
     size_t scratch_bytes = 0;             // counter + low-resolution images
     std::vector<size_t> lo_offset;        // per request, (size_t)-1 if d_i == 1
     std::vector<void *> final_out;
+    bool preview = false;                 // some request has d_r > 1
     ~BatchPlan() {
         delete bp;
         delete up;
@@ -191,6 +200,7 @@ static vdi_status plan_batch(vdi_ctx *ctx, const vdi_request *reqs, int n, Batch
             return fail(s, "request %d: %s", i, m.c_str());
         }
         if (r.vdi->ctx != ctx) return fail(VDI_ERR_INVALID_ARG, "request %d: VDI of another context", i);
+        if (r.d_r > 1) pl.preview = true;
         int vi = -1;
         for (size_t k = 0; k < vdis.size(); ++k)
             if (vdis[k] == r.vdi) vi = (int)k;
@@ -250,9 +260,9 @@ static void bind_scratch(BatchPlan &pl, char *scratch) {
         }
 }
 
-static int persistent_blocks(vdi_ctx *ctx, int ws, int bps) {
+static int persistent_blocks(vdi_ctx *ctx, int ws, int bps, bool preview) {
     int occ = 1;
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, render_fn(ws), 256, 0);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, render_fn(ws, preview), 256, 0);
     if (bps > 0) occ = std::min(occ, bps);
     return std::max(1, occ) * ctx->sm_count;
 }
@@ -260,9 +270,9 @@ static int persistent_blocks(vdi_ctx *ctx, int ws, int bps) {
 static cudaError_t enqueue_plain(vdi_ctx *ctx, BatchPlan &pl, int ws, int bps, cudaStream_t st) {
     cudaError_t e = cudaMemsetAsync(pl.bp->counter, 0, sizeof(unsigned), st);
     if (e != cudaSuccess) return e;
-    const int grid = std::min(persistent_blocks(ctx, ws, bps), std::max(1, pl.bp->total_tiles));
+    const int grid = std::min(persistent_blocks(ctx, ws, bps, pl.preview), std::max(1, pl.bp->total_tiles));
     void *args[] = {pl.bp};
-    e = cudaLaunchKernel(render_fn(ws), dim3(grid), dim3(256), args, 0, st);
+    e = cudaLaunchKernel(render_fn(ws, pl.preview), dim3(grid), dim3(256), args, 0, st);
     if (e != cudaSuccess || pl.up->n == 0) return e;
     void *uargs[] = {pl.up};
     return cudaLaunchKernel((const void *)batch_upsample_kernel, dim3(pl.up->total_tiles), dim3(256), uargs, 0, st);
@@ -326,7 +336,7 @@ static vdi_status enqueue_graph(vdi_ctx *ctx, const vdi_request *reqs, int n, Ba
         GraphEntry ge;
         if ((e = cudaMalloc(&ge.scratch, pl.scratch_bytes)) != cudaSuccess) return cuda_fail(e, "graph scratch");
         bind_scratch(pl, (char *)ge.scratch);
-        ge.grid = std::min(persistent_blocks(ctx, ws, bps), std::max(1, pl.bp->total_tiles));
+        ge.grid = std::min(persistent_blocks(ctx, ws, bps, pl.preview), std::max(1, pl.bp->total_tiles));
         cudaGraphNode_t ms = nullptr;
         cudaMemsetParams mp{};
         mp.dst = ge.scratch;
@@ -337,7 +347,7 @@ static vdi_status enqueue_graph(vdi_ctx *ctx, const vdi_request *reqs, int n, Ba
         mp.pitch = 4;
         void *args[] = {pl.bp};
         cudaKernelNodeParams kp{};
-        kp.func = (void *)render_fn(ws);
+        kp.func = (void *)render_fn(ws, pl.preview);
         kp.gridDim = dim3(ge.grid);
         kp.blockDim = dim3(256);
         kp.kernelParams = args;
@@ -371,7 +381,7 @@ static vdi_status enqueue_graph(vdi_ctx *ctx, const vdi_request *reqs, int n, Ba
         bind_scratch(pl, (char *)ge.scratch);
         void *args[] = {pl.bp};
         cudaKernelNodeParams kp{};
-        kp.func = (void *)render_fn(ws);
+        kp.func = (void *)render_fn(ws, pl.preview);
         kp.gridDim = dim3(ge.grid);
         kp.blockDim = dim3(256);
         kp.kernelParams = args;
@@ -458,11 +468,13 @@ VDI_API vdi_status vdi_autotune_batch(vdi_ctx *ctx, const vdi_request *reqs, int
     cudaEventCreate(&e1);
     vdi_batch_opts winner = {0, 0, 0};
     float wms = INFINITY;
-    int occ_max = 1;
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ_max, render_fn(0), 256, 0);
+    bool preview = false;
+    for (int i = 0; i < n; ++i) preview = preview || reqs[i].d_r > 1;
     vdi_status s = VDI_OK;
-    for (int ws = 0; ws <= 3 && s == VDI_OK; ++ws)
-        for (int bps = 1; bps <= std::max(1, occ_max) && s == VDI_OK; bps *= 2) {
+    for (int ws = 0; ws <= 3 && s == VDI_OK; ++ws) {
+        int occ_max = 1;
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ_max, render_fn(ws, preview), 256, 0);
+        for (int bps = 1; bps <= std::max(1, occ_max) && s == VDI_OK; ++bps) {
             vdi_batch_opts o = {ws, bps, 0};
             s = render_batch(ctx, reqs, n, &o, st);  // warm-up
             if (s != VDI_OK) break;
@@ -482,6 +494,7 @@ VDI_API vdi_status vdi_autotune_batch(vdi_ctx *ctx, const vdi_request *reqs, int
                 winner = o;
             }
         }
+    }
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
     if (s != VDI_OK) return s;
