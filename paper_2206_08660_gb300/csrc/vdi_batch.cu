@@ -101,9 +101,9 @@ __global__ void __launch_bounds__(256, PREVIEW ? 3 : 4) batch_render_kernel(cons
             if (setup_ray(q.c, px, py, v.w, v.h, ray)) {
                 if (PREVIEW && q.c.d_r > 1) {
                     if (v.fmt == 0)
-                        march_preview<0, kSearchAlg2, true>(v, q.c, ray, acc);
+                        march_preview<0, true, 0>(v, q.c, ray, acc);
                     else
-                        march_preview<1, kSearchAlg2, true>(v, q.c, ray, acc);
+                        march_preview<1, true, 0>(v, q.c, ray, acc);
                 } else {
                     if (v.fmt == 0)
                         march_exact<0, kSearchAlg2, true>(v, ray, acc, nl, nsg);

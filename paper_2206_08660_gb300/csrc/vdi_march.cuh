@@ -516,7 +516,15 @@ __device__ __forceinline__ void march_exact_ess(const DevVdi &v, Ray &r, Accum &
 // look each one up in its list (Algorithm 2 search, seeded by the previous
 // sample) and composite with opacity corrected by the spacing.
 // ---------------------------------------------------------------------------
-template <int FMT, int MODE, bool ERT>
+// PW: depth records requested at once when a sample looks for its
+// supersegment (0: Algorithm 2 with the index carried between samples).  Preview samples lie far apart along the ray, so the index
+// carried from the previous sample seldom helps and Algorithm 2's dependent
+// probes would each cost a memory round trip; instead the list's depth
+// records are read PW pairs at a time and the first slot whose back is at or
+// beyond the sample's depth is picked (the same result as Algorithm 2).  A
+// wide probe suits launches with few rays, a narrow one (fewer registers,
+// more resident warps) launches with many.
+template <int FMT, bool ERT, int PW>
 __device__ __forceinline__ void march_preview(const DevVdi &v, const ViewConsts &c, Ray &r,
                                               Accum &acc) {
     const float hw = 0.5f * (float)v.w, hh = 0.5f * (float)v.h;
@@ -536,7 +544,7 @@ __device__ __forceinline__ void march_preview(const DevVdi &v, const ViewConsts 
     int ez = inc ? cz + 1 : cz;  // index of the next slab edge met
     float sz = (dz != 0.f) ? (v.edges[ez] - z0) * idz : INFINITY;
     const float w0 = r.w0, w1 = r.w1, dw = r.dw;
-    int p = -1, plist = -1;
+    int p = -1, plist = -1;  // Algorithm 2's carried index (PW == 0)
     PairCache pc;
     pc.k = -1;
     ColourCache<FMT> cc;
@@ -574,12 +582,37 @@ __device__ __forceinline__ void march_preview(const DevVdi &v, const ViewConsts 
                     }
                     const float2 rg = __ldg(v.range + li);
                     if (nz < rg.x || nz > rg.y) continue;  // outside every supersegment of the list
-                    const int j = first_inc<MODE>(v, li, nz, p, pc);
-                    p = min(j, v.nsp - 1);
+                    int j = v.nsp;
+                    float fj = INFINITY;
+                    if (PW == 0) {
+                        j = first_inc<kSearchAlg2>(v, li, nz, p, pc);
+                        p = min(j, v.nsp - 1);
+                        if (j < v.nsp) {
+                            float b;
+                            get_fb(pc, v, li, j, fj, b);
+                        }
+                    }
+                    const int npairs = v.nsp >> 1;
+                    for (int k0 = 0; PW > 0 && k0 < npairs && j == v.nsp; k0 += (PW > 0 ? PW : 1)) {
+                        float4 d[PW > 0 ? PW : 1];
+#pragma unroll
+                        for (int i = 0; i < PW; ++i)
+                            if (k0 + i < npairs) d[i] = ld_depth_pair(v, k0 + i, li);
+#pragma unroll
+                        for (int i = PW - 1; i >= 0; --i)
+                            if (k0 + i < npairs) {
+                                if (d[i].w >= nz) {
+                                    j = 2 * (k0 + i) + 1;
+                                    fj = d[i].z;
+                                }
+                                if (d[i].y >= nz) {
+                                    j = 2 * (k0 + i);
+                                    fj = d[i].x;
+                                }
+                            }
+                    }
                     if (j < v.nsp) {
-                        float f, b;
-                        get_fb(pc, v, li, j, f, b);
-                        if (f <= nz) {
+                        if (fj <= nz) {
                             add_piece(acc, get_colour<FMT>(cc, v, li, j), spacing);
                             if (ERT && acc.T <= kErtT) return;
                         }

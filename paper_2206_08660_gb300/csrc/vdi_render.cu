@@ -18,7 +18,8 @@ namespace vdi {
 
 // PATH: 0 = exact walk over every list (the default), 1 = exact walk with
 // empty-space skipping over the count grid, 2 = ray-subsampled preview
-// (D_R > 1), 3 = exact walk with range-block skipping.
+// (D_R > 1), 3 = exact walk with range-block skipping, 4 = ray-subsampled
+// preview with a wide supersegment probe (for launches with few rays).
 template <int FMT, int MODE, bool ERT, int WX, int PATH>
 __global__ void __launch_bounds__(256) render_kernel(const ViewConsts c, const DevVdi v, void *out,
                                                      int out_fmt, uint32_t *ray_lists,
@@ -32,7 +33,9 @@ __global__ void __launch_bounds__(256) render_kernel(const ViewConsts c, const D
     Ray r;
     if (setup_ray(c, px, py, v.w, v.h, r)) {
         if (PATH == 2)
-            march_preview<FMT, MODE, ERT>(v, c, r, acc);
+            march_preview<FMT, ERT, 3>(v, c, r, acc);
+        else if (PATH == 4)
+            march_preview<FMT, ERT, 10>(v, c, r, acc);
         else if (PATH == 1)
             march_exact_ess<FMT, MODE, ERT>(v, r, acc, nl, nsg);
         else if (PATH == 3)
@@ -137,7 +140,13 @@ static cudaError_t launch_ws(const ViewConsts &c, const DevVdi &v, void *out, in
 template <int FMT, int MODE>
 static cudaError_t launch_m(const ViewConsts &c, const DevVdi &v, void *out, int out_fmt, uint32_t *rl,
                             uint32_t *rs, int warp_shape, bool ert, bool ess, bool blocks, cudaStream_t st) {
-    if (c.d_r > 1) return launch_ws<FMT, MODE, true, 2>(c, v, out, out_fmt, rl, rs, warp_shape, st);
+    if (c.d_r > 1) {
+        // previews ignore the search mode (their samples use a wide probe); a
+        // launch of up to about two waves of rays takes the widest probe
+        if ((long long)c.W * c.H <= 300000)
+            return launch_ws<FMT, kSearchAlg2, true, 4>(c, v, out, out_fmt, rl, rs, warp_shape, st);
+        return launch_ws<FMT, kSearchAlg2, true, 2>(c, v, out, out_fmt, rl, rs, warp_shape, st);
+    }
     // per-ray counters count whole lists, so they come from the walk over every list
     if (!ert) return launch_ws<FMT, MODE, false, 0>(c, v, out, out_fmt, rl, rs, warp_shape, st);
     if (rl || rs) return launch_ws<FMT, MODE, true, 0>(c, v, out, out_fmt, rl, rs, warp_shape, st);
