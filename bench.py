@@ -168,6 +168,20 @@ class ClockSampler:
         return {"sm_mhz": float(np.median(sm)), "sm_max_mhz": smax, "reasons": sorted(reasons), "samples": len(sm)}
 
 
+def cpu_model() -> str:
+    """The host CPU's model name (lscpu), or the machine type."""
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for line in out.splitlines():
+            if line.startswith("Model name:"):
+                return line.split(":", 1)[1].strip()
+    except Exception:
+        pass
+    import platform
+
+    return platform.machine()
+
+
 def max_over_ranks(x: float, device=None) -> float:
     """The largest value of x over the ranks of the default process group (x itself
     when there is none): the benchmark's time per step is the slowest rank's."""
@@ -353,6 +367,20 @@ def serving_leg(V, torch, ctx, dev, cfg=SERVING):
         V.vdi_render(vdis32[slot], cam, W, H, d_i, d_r, outs[(W, H)], V.VDI_F32)
     torch.cuda.synchronize()
     single_rps = len(sat) / (time.monotonic() - t0)
+    # accuracy of the FP16-colour VDIs against the FP32 ones on the same requests
+    errs = []
+    for k in range(4):
+        v16 = gen(k, V.VDI_F16)[0]
+        for (slot, cam, W, H, d_i, d_r) in [r for r in sat if r[0] == k][:4]:
+            a = torch.empty((H, W, 4), dtype=torch.float32, device=dev)
+            b = torch.empty((H, W, 4), dtype=torch.float32, device=dev)
+            V.vdi_render(v16, cam, W, H, d_i, d_r, a, V.VDI_F32)
+            V.vdi_render(vdis32[k], cam, W, H, d_i, d_r, b, V.VDI_F32)
+            torch.cuda.synchronize()
+            errs.append((a - b).abs().amax(dim=2).flatten().cpu().numpy())
+        V.vdi_destroy(v16)
+    e = np.concatenate(errs) if errs else np.zeros(1)
+    fp16_vs_fp32 = {"max": float(e.max()), "q999": float(np.quantile(e, 0.999)), "requests": len(errs)}
     for v in vdis32:
         V.vdi_destroy(v)
     del vol_d
@@ -361,6 +389,7 @@ def serving_leg(V, torch, ctx, dev, cfg=SERVING):
                         "360p:720p:1080p = 1:2:1, deviation U[0,45] deg, D_I,D_R in {1,2}, one VDI replaced "
                         "every 2 s from a side stream, 24 GB budget",
             "open_loop": open_loop,
+            "fp16_vs_fp32_pixel_error": fp16_vs_fp32,
             "saturated": {"batched_fp16_server_rps": batched_rps, "one_view_per_launch_fp32_rps": single_rps,
                           "requests": len(sat)}}
 
@@ -695,8 +724,17 @@ def main():
             rng = np.random.default_rng(0)
             R = leg.rays_for_budget(args.cpu_budget, rng)
             _, full = leg.run(R, rng)
+            # one core on a tenth of the sample, for the per-core rate
+            threads = leg.threads
+            leg.threads = 1
+            R1 = max(256, R // 10)
+            _, full1 = leg.run(R1, rng)
+            leg.threads = threads
             result["cpu_baseline"] = {"value": frames_per_step / full, "unit": "frames/s", "cores": leg.threads,
-                                      "kind": "oracle", "sample": leg.sample_text(R)}
+                                      "kind": "oracle", "sample": leg.sample_text(R),
+                                      "cpu_model": cpu_model(), "rays_per_s": rays / full,
+                                      "one_core_frames_per_s": frames_per_step / full1,
+                                      "one_core_sample": f"{R1} random rays from each frame, one thread"}
         except Exception as e:  # the oracle must not take the GPU number down with it
             result["cpu_baseline"] = {"value": None, "unit": "frames/s", "cores": os.cpu_count(),
                                       "kind": "oracle", "sample": f"failed: {e}"}
