@@ -470,7 +470,8 @@ def main():
             return
         leg = OracleLeg(wl, vol, bmin, bmax, u, cam_o, views)
         rng = np.random.default_rng(0)
-        R = leg.rays_for_budget(2.0, rng)
+        # each step a bounded sample: the whole run stays near two minutes of oracle work
+        R = leg.rays_for_budget(min(2.0, 120.0 / max(1, args.steps + args.warmup)), rng)
         t_all = []
         for i in range(args.warmup + args.steps):
             _, full = leg.run(R, rng)
