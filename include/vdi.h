@@ -99,7 +99,8 @@ typedef struct {
 } vdi_layout;
 
 typedef struct {
-    int search;          /* VDI_SEARCH_*; default VDI_SEARCH_ALG2 */
+    int search;          /* VDI_SEARCH_*; default VDI_SEARCH_ALG2 (the exact path; D_R previews read
+                            a list's depth records several pairs at a time whatever the mode) */
     int no_ert;          /* 1: keep compositing past full opacity (for exact counters) */
     uint32_t *ray_lists; /* nullable device [H'][W']: lists traversed with positive length per ray */
     uint32_t *ray_segs;  /* nullable device [H'][W']: supersegment pieces of positive length per ray */
