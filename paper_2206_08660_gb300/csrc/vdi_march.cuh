@@ -179,8 +179,10 @@ struct Seg {
 // Algorithm 2 (seeded with p, the last index met in the previous list),
 // adjacency walk, Eq. 2 per piece, front-to-back compositing.  Returns true
 // once the ray is opaque (early termination).
-// PRE: the caller has already loaded the list's range (rg_pre).
-template <int FMT, int MODE, bool ERT, bool TOUCH, bool PRE = false>
+// PRE: the caller has already loaded the list's range (rg_pre).  DIR: the
+// sign of the ray's depth slope when the caller knows it (+1 / -1), 0 when it
+// is decided at run time; the result is the same, the known sign saves work.
+template <int FMT, int MODE, bool ERT, bool TOUCH, bool PRE = false, int DIR = 0>
 __device__ __forceinline__ bool process_list(const DevVdi &v, const Seg &g, int li, float s_in, float s_out,
                                              int &p, Accum &acc, uint32_t &n_lists, uint32_t &n_segs,
                                              uint32_t *bm, bool &hot, float2 rg_pre = make_float2(0.f, 0.f)) {
@@ -205,11 +207,16 @@ __device__ __forceinline__ bool process_list(const DevVdi &v, const Seg &g, int 
             mark_word<TOUCH>(bm, range_word_base(v) + 2 * (size_t)li);
             mark_word<TOUCH>(bm, range_word_base(v) + 2 * (size_t)li + 1);
         }
-        hot = !(fmaxf(d_in, d_out) < rg.x || fminf(d_in, d_out) > rg.y);
+        if (DIR > 0)
+            hot = !(d_out < rg.x || d_in > rg.y);
+        else if (DIR < 0)
+            hot = !(d_in < rg.x || d_out > rg.y);
+        else
+            hot = !(fmaxf(d_in, d_out) < rg.x || fminf(d_in, d_out) > rg.y);
         if (!hot) return false;
     }
     int last = -1, first;
-    if (g.dz >= 0.f) {
+    if (DIR > 0 || (DIR == 0 && g.dz >= 0.f)) {
         first = first_inc<MODE, TOUCH>(v, li, d_in, p, pc, bm);
         for (int j = first; j < v.nsp; ++j) {
             float f, b;
@@ -279,7 +286,7 @@ __device__ __forceinline__ Seg seg_of(const Ray &r) {
 // leaves the block.  The image is the same; the skipped lists are not
 // counted by the per-ray list counter, so counters use BLOCKS = false.
 // ---------------------------------------------------------------------------
-template <int FMT, int MODE, bool ERT, bool TOUCH = false, bool BLOCKS = false>
+template <int FMT, int MODE, bool ERT, bool TOUCH = false, bool BLOCKS = false, int DIR = 0>
 __device__ __forceinline__ void march_exact(const DevVdi &v, Ray &r, Accum &acc, uint32_t &n_lists,
                                             uint32_t &n_segs, uint32_t *bm = nullptr) {
     // list-grid position relative to the integer origin (ox, oy): boundary k is
@@ -320,8 +327,8 @@ __device__ __forceinline__ void march_exact(const DevVdi &v, Ray &r, Accum &acc,
             float2 rg_next = rg;
             if (nin && s_out < 1.f) rg_next = __ldg(v.range + nli);  // not when the ray ends in this list
             if (s_out > s_in) {
-                if (process_list<FMT, MODE, ERT, TOUCH, true>(v, g, li, s_in, s_out, p, acc, n_lists, n_segs, bm,
-                                                              hot, rg))
+                if (process_list<FMT, MODE, ERT, TOUCH, true, DIR>(v, g, li, s_in, s_out, p, acc, n_lists, n_segs,
+                                                                   bm, hot, rg))
                     break;
             }
             if (s_out >= 1.f || !nin) break;

@@ -40,8 +40,10 @@ __global__ void __launch_bounds__(256) render_kernel(const ViewConsts c, const D
             march_exact_ess<FMT, MODE, ERT>(v, r, acc, nl, nsg);
         else if (PATH == 3)
             march_exact<FMT, MODE, ERT, false, true>(v, r, acc, nl, nsg);
+        else if (r.dz >= 0.f)  // two copies of the walk, one per depth direction
+            march_exact<FMT, MODE, ERT, false, false, 1>(v, r, acc, nl, nsg);
         else
-            march_exact<FMT, MODE, ERT>(v, r, acc, nl, nsg);
+            march_exact<FMT, MODE, ERT, false, false, -1>(v, r, acc, nl, nsg);
     }
     const size_t idx = (size_t)py * c.W + px;
     store_px(out, out_fmt, idx, acc);
