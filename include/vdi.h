@@ -253,6 +253,8 @@ typedef struct {
     int W, H, d_i, d_r;  /* as in vdi_render */
     void *out;           /* DEVICE [H][W][4] of out_fmt */
     int out_fmt;
+    int Wr, Hr;          /* rays rendered, as in vdi_render_scaled (1..W, 1..H; d_i is then ignored);
+                            0, 0: ceil(W / d_i) x ceil(H / d_i) */
 } vdi_request;
 
 typedef struct {
@@ -307,6 +309,9 @@ typedef struct {
     int slot;              /* resident VDI slot */
     vdi_camera view;
     int W, H, d_i, d_r, out_fmt;
+    int Wr, Hr;            /* rays rendered (as in vdi_request); 0, 0: from d_i.  A client that
+                              keeps a frame rate with the preview controller (vdi_pi_*) passes
+                              the ray counts vdi_pi_update returned */
 } vdi_view_request;
 
 typedef struct {

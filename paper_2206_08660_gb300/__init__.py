@@ -75,7 +75,7 @@ class VdiGenParams(C.Structure):
 
 class VdiRequest(C.Structure):
     _fields_ = [("vdi", C.c_void_p), ("view", VdiCamera), ("W", C.c_int), ("H", C.c_int), ("d_i", C.c_int),
-                ("d_r", C.c_int), ("out", C.c_void_p), ("out_fmt", C.c_int)]
+                ("d_r", C.c_int), ("out", C.c_void_p), ("out_fmt", C.c_int), ("Wr", C.c_int), ("Hr", C.c_int)]
 
 
 class VdiBatchOpts(C.Structure):
@@ -89,7 +89,7 @@ class VdiServerConfig(C.Structure):
 
 class VdiViewRequest(C.Structure):
     _fields_ = [("slot", C.c_int), ("view", VdiCamera), ("W", C.c_int), ("H", C.c_int), ("d_i", C.c_int),
-                ("d_r", C.c_int), ("out_fmt", C.c_int)]
+                ("d_r", C.c_int), ("out_fmt", C.c_int), ("Wr", C.c_int), ("Hr", C.c_int)]
 
 
 class VdiTicketInfo(C.Structure):
@@ -425,10 +425,11 @@ def touched_bytes(vdi, cam: VdiCamera, W, H, stream=None) -> int:
     return int(np.unpackbits(b).sum()) * 4
 
 
-def request(vdi, cam: VdiCamera, W, H, d_i, d_r, out, out_fmt=VDI_F32) -> VdiRequest:
+def request(vdi, cam: VdiCamera, W, H, d_i, d_r, out, out_fmt=VDI_F32, Wr=0, Hr=0) -> VdiRequest:
     r = VdiRequest()
     r.vdi, r.view, r.W, r.H, r.d_i, r.d_r = vdi, cam, int(W), int(H), int(d_i), int(d_r)
     r.out, r.out_fmt = _dptr(out), int(out_fmt)
+    r.Wr, r.Hr = int(Wr), int(Hr)
     return r
 
 
@@ -469,10 +470,11 @@ def vdi_server_set_vdi(server, slot, vdi, ready_stream=None):
     _check(load().vdi_server_set_vdi(server, int(slot), vdi, _stream(ready_stream)))
 
 
-def view_request(slot, cam: VdiCamera, W, H, d_i=1, d_r=1, out_fmt=VDI_F16) -> VdiViewRequest:
+def view_request(slot, cam: VdiCamera, W, H, d_i=1, d_r=1, out_fmt=VDI_F16, Wr=0, Hr=0) -> VdiViewRequest:
     r = VdiViewRequest()
     r.slot, r.view, r.W, r.H, r.d_i, r.d_r, r.out_fmt = int(slot), cam, int(W), int(H), int(d_i), int(d_r), \
         int(out_fmt)
+    r.Wr, r.Hr = int(Wr), int(Hr)
     return r
 
 

@@ -48,4 +48,16 @@ cudaError_t launch_block_range(const DevVdi &v, float2 *brange, cudaStream_t st)
 // row of lists) unless the autotuner recorded a better one
 inline int default_warp_shape(const vdi_t *, int, int) { return 3; }  // 4 x 8 pixels per warp
 
+// rays a request renders: explicit (Wr, Hr) when given, else ceil(W / d_i) x ceil(H / d_i)
+template <class R>
+inline void request_rays(const R &r, int &Wr, int &Hr) {
+    if (r.Wr > 0 && r.Hr > 0) {
+        Wr = r.Wr;
+        Hr = r.Hr;
+    } else {
+        Wr = (r.W + r.d_i - 1) / r.d_i;
+        Hr = (r.H + r.d_i - 1) / r.d_i;
+    }
+}
+
 }  // namespace vdi

@@ -32,7 +32,7 @@ constexpr int kMaxBatchVdi = VDI_BATCH_MAX_VDIS;
 
 struct BatchReq {
     ViewConsts c;
-    void *out;       // final image, or the low-resolution scratch when d_i > 1
+    void *out;       // final image, or the low-resolution scratch when fewer rays than pixels
     int out_fmt;
     int vdi;         // index into BatchParams::vdis
     int tiles_x;
@@ -172,7 +172,7 @@ struct BatchPlan {
     BatchParams *bp = nullptr;  // host copies (large structs live on the heap)
     UpParams *up = nullptr;
     size_t scratch_bytes = 0;             // counter + low-resolution images
-    std::vector<size_t> lo_offset;        // per request, (size_t)-1 if d_i == 1
+    std::vector<size_t> lo_offset;        // per request, (size_t)-1 if it renders every pixel
     std::vector<void *> final_out;
     bool preview = false;                 // some request has d_r > 1
     ~BatchPlan() {
@@ -199,6 +199,8 @@ static vdi_status plan_batch(vdi_ctx *ctx, const vdi_request *reqs, int n, Batch
             const std::string m = vdi_last_error_message();
             return fail(s, "request %d: %s", i, m.c_str());
         }
+        if ((r.Wr != 0 || r.Hr != 0) && (r.Wr < 1 || r.Hr < 1 || r.Wr > r.W || r.Hr > r.H))
+            return fail(VDI_ERR_INVALID_ARG, "request %d: rays %dx%d for image %dx%d", i, r.Wr, r.Hr, r.W, r.H);
         if (r.vdi->ctx != ctx) return fail(VDI_ERR_INVALID_ARG, "request %d: VDI of another context", i);
         if (r.d_r > 1) pl.preview = true;
         int vi = -1;
@@ -211,7 +213,8 @@ static vdi_status plan_batch(vdi_ctx *ctx, const vdi_request *reqs, int n, Batch
             vdis.push_back(r.vdi);
             pl.bp->vdis[vi] = r.vdi->dv;
         }
-        const int Wr = div_up(r.W, r.d_i), Hr = div_up(r.H, r.d_i);
+        int Wr, Hr;
+        request_rays(r, Wr, Hr);
         BatchReq &q = pl.bp->reqs[i];
         s = make_view_consts(r.vdi, &r.view, Wr, Hr, r.d_r, &q.c);
         if (s != VDI_OK) {
@@ -223,7 +226,7 @@ static vdi_status plan_batch(vdi_ctx *ctx, const vdi_request *reqs, int n, Batch
         q.tile_base = tiles;
         tiles += q.tiles_x * div_up(Hr, 8);
         pl.final_out[i] = r.out;
-        if (r.d_i == 1) {
+        if (Wr == r.W && Hr == r.H) {
             q.out = r.out;
             q.out_fmt = r.out_fmt;
         } else {
@@ -306,19 +309,25 @@ static BatchCache &cache_of(vdi_ctx *ctx) {
 static std::string shape_key(const vdi_request *reqs, int n, const BatchPlan &pl, int ws, int bps, cudaStream_t st) {
     std::string k = std::to_string((unsigned long long)(uintptr_t)st) + "|" + std::to_string(ws) + "|" +
                     std::to_string(bps) + "|" + std::to_string(pl.scratch_bytes);
-    for (int i = 0; i < n; ++i)
-        k += "|" + std::to_string(reqs[i].W) + "x" + std::to_string(reqs[i].H) + "/" + std::to_string(reqs[i].d_i) +
-             "/" + std::to_string(reqs[i].d_r);
+    for (int i = 0; i < n; ++i) {
+        int Wr, Hr;
+        request_rays(reqs[i], Wr, Hr);
+        k += "|" + std::to_string(reqs[i].W) + "x" + std::to_string(reqs[i].H) + "/" + std::to_string(Wr) + "x" +
+             std::to_string(Hr) + "/" + std::to_string(reqs[i].d_r);
+    }
     return k;
 }
 
 // batch signature used by the autotuner: resolutions, previews and formats
 static std::string tune_key(const vdi_request *reqs, int n) {
     std::vector<std::string> parts;
-    for (int i = 0; i < n; ++i)
-        parts.push_back(std::to_string(reqs[i].W) + "x" + std::to_string(reqs[i].H) + "/" +
-                        std::to_string(reqs[i].d_i) + "/" + std::to_string(reqs[i].d_r) + "/" +
+    for (int i = 0; i < n; ++i) {
+        int Wr, Hr;
+        request_rays(reqs[i], Wr, Hr);
+        parts.push_back(std::to_string(reqs[i].W) + "x" + std::to_string(reqs[i].H) + "/" + std::to_string(Wr) + "x" +
+                        std::to_string(Hr) + "/" + std::to_string(reqs[i].d_r) + "/" +
                         std::to_string(reqs[i].vdi->dv.nsp) + "/" + std::to_string(reqs[i].vdi->dv.fmt));
+    }
     std::sort(parts.begin(), parts.end());
     std::string k;
     for (auto &p : parts) k += p + ";";

@@ -98,7 +98,9 @@ static size_t align256(size_t b) { return (b + 255) & ~(size_t)255; }
 // admission cost: the image plus the low-resolution scratch of a D_I preview
 static size_t request_bytes(const vdi_view_request &r) {
     size_t b = align256(image_bytes(r));
-    if (r.d_i > 1) b += align256((size_t)div_up(r.W, r.d_i) * div_up(r.H, r.d_i) * 16);
+    int Wr, Hr;
+    request_rays(r, Wr, Hr);
+    if (Wr != r.W || Hr != r.H) b += align256((size_t)Wr * Hr * 16);
     return b;
 }
 
@@ -191,6 +193,8 @@ static bool launch_one(vdi_server *s) {
         q.H = r.H;
         q.d_i = r.d_i;
         q.d_r = r.d_r;
+        q.Wr = r.Wr;
+        q.Hr = r.Hr;
         q.out = img;
         q.out_fmt = r.out_fmt;
         reqs.push_back(q);
@@ -307,6 +311,8 @@ VDI_API vdi_status vdi_server_submit(vdi_server *s, const vdi_view_request *req,
     if (req->W < 1 || req->H < 1 || req->W > 16384 || req->H > 16384 || req->d_i < 1 || req->d_i > 16 ||
         req->d_r < 1 || req->d_r > 16 || (req->out_fmt != VDI_F32 && req->out_fmt != VDI_F16))
         return fail(VDI_ERR_INVALID_ARG, "bad request");
+    if ((req->Wr != 0 || req->Hr != 0) && (req->Wr < 1 || req->Hr < 1 || req->Wr > req->W || req->Hr > req->H))
+        return fail(VDI_ERR_INVALID_ARG, "rays %dx%d for image %dx%d", req->Wr, req->Hr, req->W, req->H);
     {
         std::lock_guard<std::mutex> g(s->mu);
         const uint64_t id = s->next_ticket++;

@@ -130,3 +130,31 @@ def test_batch_rejects_bad_batches(V, ctx, vdis):
     reqs[1].out = None
     with pytest.raises(V.VdiError):
         V.vdi_render_batch(ctx, reqs)
+
+
+@pytest.mark.parametrize("use_graph", [False, True])
+def test_batch_with_explicit_ray_counts(V, ctx, vdis, use_graph):
+    """Requests that name their ray counts (fractional image-space scales, as the
+    preview controller picks them) equal vdi_render_scaled, graph replays included."""
+    rng = np.random.default_rng(9)
+    reqs, outs = [], []
+    for i in range(12):
+        case, vdi = vdis[i % len(vdis)]
+        W, H = [(96, 64), (75, 53), (128, 72)][i % 3]
+        Wr, Hr = int(rng.integers(1, W + 1)), int(rng.integers(1, H + 1))
+        d_r = 1 + (i % 2)
+        fmt = i % 2
+        cam = S.orbit_camera(case.bmin, case.bmax, W / H, az_deg=float(rng.uniform(-30, 30)), el_deg=15.0)
+        out = torch.zeros((H, W, 4), dtype=torch.float32 if fmt == 0 else torch.float16, device="cuda")
+        reqs.append(V.request(vdi, V.camera(cam.view, cam.proj), W, H, 1, d_r, out, fmt, Wr=Wr, Hr=Hr))
+        outs.append((out, cam, vdi, W, H, Wr, Hr, d_r, fmt))
+    for rep in range(2):
+        for o in outs:
+            o[0].zero_()
+        V.vdi_render_batch(ctx, reqs, use_graph=use_graph)
+        torch.cuda.synchronize()
+        for (out, cam, vdi, W, H, Wr, Hr, d_r, fmt) in outs:
+            ref = torch.zeros_like(out)
+            V.vdi_render_scaled(vdi, V.camera(cam.view, cam.proj), W, H, Wr, Hr, d_r, ref, fmt)
+            torch.cuda.synchronize()
+            assert torch.equal(out, ref), (W, H, Wr, Hr, d_r, fmt)

@@ -134,3 +134,45 @@ def test_replacement_waits_for_its_producer_and_bounded_wait_times_out(V, ctx):
     finally:
         V.vdi_server_destroy(srv)
         V.vdi_destroy(ref2)
+
+
+def test_preview_controller_session_through_the_server(V, ctx):
+    """A client keeps a frame-time target with the preview controller: each
+    request carries the ray counts the controller chose from the previous
+    request's service time, and every result equals vdi_render_scaled at those
+    counts."""
+    case, vdi = make_vdi(V, ctx, 7, 1)
+    ref_vdi = V.vdi_create(ctx, case.gpu_desc(V, 1), case.vdi.rgba, case.vdi.depth, case.vdi.counts)
+    srv = V.vdi_server_create(ctx, 1 << 28, 4, 2, 1)
+    try:
+        V.vdi_server_set_vdi(srv, 0, vdi)
+        W, H = 320, 200
+        cam = S.orbit_camera(case.bmin, case.bmax, W / H, az_deg=10.0, el_deg=15.0)
+        t = V.vdi_server_submit(srv, V.view_request(0, V.camera(cam.view, cam.proj), W, H, 1, 2, V.VDI_F16))
+        info = V.vdi_server_wait(srv, t, 30.0)
+        V.vdi_server_release(srv, t)
+        # a target below the full-resolution service time pulls the scale down
+        pi = V.PiController(0.5 * (info.t_done - info.t_start) * 1e3, W, H, scale_min=0.2)
+        s, Wr, Hr = pi.current()
+        seen = set()
+        for k in range(12):
+            cam = S.orbit_camera(case.bmin, case.bmax, W / H, az_deg=10.0 + 2.0 * k, el_deg=15.0)
+            t = V.vdi_server_submit(srv, V.view_request(0, V.camera(cam.view, cam.proj), W, H, 1, 2,
+                                                        V.VDI_F16, Wr=Wr, Hr=Hr))
+            info = V.vdi_server_wait(srv, t, 30.0)
+            assert info.status == 0
+            got = download_image(V, srv, t, W, H, 1)
+            V.vdi_server_release(srv, t)
+            ref = torch.zeros((H, W, 4), dtype=torch.float16, device="cuda")
+            V.vdi_render_scaled(ref_vdi, V.camera(cam.view, cam.proj), W, H, Wr, Hr, 2, ref, V.VDI_F16)
+            torch.cuda.synchronize()
+            assert torch.equal(got, ref), (k, Wr, Hr)
+            seen.add((Wr, Hr))
+            s, Wr, Hr = pi.update((info.t_done - info.t_start) * 1e3)
+        assert len(seen) >= 2 and min(w for w, _ in seen) < W  # the controller moved the ray counts
+        with pytest.raises(V.VdiError):
+            V.vdi_server_submit(srv, V.view_request(0, V.camera(cam.view, cam.proj), W, H, 1, 1, V.VDI_F16,
+                                                    Wr=W + 1, Hr=H))
+    finally:
+        V.vdi_server_destroy(srv)
+        V.vdi_destroy(ref_vdi)
