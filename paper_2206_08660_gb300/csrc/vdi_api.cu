@@ -266,6 +266,16 @@ vdi_status make_view_consts(const vdi_t *v, const vdi_camera *cam, int W, int H,
     c->a_affine = a_aff;
     c->b_affine = b_aff;
     c->frustum_clip = v->box_in_frustum ? 0 : 1;
+    // V_N's rays start at V_O's eye when that eye's clip coordinates x, y, w
+    // vanish: each ray then has one V_O NDC position and stays in one list
+    {
+        double bscale = 0.0;
+        for (int k = 0; k < 4; ++k) bscale = fmax(bscale, fabs(b0[k]) + fabs(bx[k]) * W + fabs(by[k]) * H);
+        c->single_list = (!a_aff && fabs(a0[0]) <= 1e-9 * bscale && fabs(a0[1]) <= 1e-9 * bscale &&
+                          fabs(a0[3]) <= 1e-9 * bscale)
+                             ? 1
+                             : 0;
+    }
     for (int k = 0; k < 3; ++k) {
         c->O0[k] = (float)O0[k];
         c->Ox[k] = (float)Ox[k];

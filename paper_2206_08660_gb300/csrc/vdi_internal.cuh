@@ -64,6 +64,7 @@ struct ViewConsts {
     double GB0[3], GBx[3], GBy[3];
     int a_affine, b_affine;
     int frustum_clip;   // 0 when the volume box lies inside V_O's frustum
+    int single_list;    // 1 when V_N's eye is V_O's eye: every ray stays in one list
     float O0[3], Ox[3], Oy[3];
     float D0[3], Dx[3], Dy[3];
     float t_lo, t_hi;

@@ -408,6 +408,101 @@ __device__ __forceinline__ void march_exact(const DevVdi &v, Ray &r, Accum &acc,
 }
 
 // ---------------------------------------------------------------------------
+// Views from V_O's own eye (Section 4.1 at zero deviation): every ray projects
+// to one point of V_O's image plane and stays in one list.  A ray that the
+// list walk would treat as exactly one list over s in [0, 1] is composited
+// here with the list's first PF slot pairs (depth and colour records)
+// requested at once, instead of one dependent round trip per pair; its
+// arithmetic is process_list's, so the image is the same.  Any other ray
+// takes the list walk.
+// ---------------------------------------------------------------------------
+template <int FMT, int MODE, bool ERT>
+__device__ __forceinline__ void march_single(const DevVdi &v, Ray &r, Accum &acc, uint32_t &n_lists,
+                                             uint32_t &n_segs) {
+    constexpr int PF = 4;
+    const int ox = r.ox, oy = r.oy;
+    const float dgx = r.dgx, dgy = r.dgy;
+    const int ix = min(max(ox, 0), v.w - 1), iy = min(max(oy, 0), v.h - 1);
+    // the walk's first crossings, in the walk's own arithmetic
+    const float idgx = rcp_fast(dgx), idgy = rcp_fast(dgy);
+    const float cx0 = -r.fx0 * idgx, cy0 = -r.fy0 * idgy;
+    const float fbx = (float)(ix + (dgx > 0.f ? 1 : 0) - ox), fby = (float)(iy + (dgy > 0.f ? 1 : 0) - oy);
+    const float sx = (dgx != 0.f) ? fmaf(fbx, idgx, cx0) : INFINITY;
+    const float sy = (dgy != 0.f) ? fmaf(fby, idgy, cy0) : INFINITY;
+    if (!(fminf(sx, sy) >= 1.f) || !(r.dz >= 0.f)) {
+        march_exact<FMT, MODE, ERT>(v, r, acc, n_lists, n_segs);
+        return;
+    }
+    const Seg g = seg_of(r);
+    const int li = iy * v.w + ix;
+    const float d_in = fmaf(0.f, g.dz, g.z0), d_out = fmaf(1.f, g.dz, g.z0);
+    ++n_lists;
+    const float2 rg = __ldg(v.range + li);
+    const int npairs = v.nsp >> 1;
+    float4 dp[PF];
+    uint4 cq[PF];
+#pragma unroll
+    for (int k = 0; k < PF; ++k)
+        if (k < npairs) {
+            dp[k] = ld_depth_pair(v, k, li);
+            if (FMT == 1) cq[k] = __ldg(reinterpret_cast<const uint4 *>(v.colour) + (k * v.nl32 + li));
+        }
+    if (d_out < rg.x || d_in > rg.y) return;
+    // slots in order; those with b < d_in lie before the first one met (b is sorted)
+    ColourCache<FMT> cc;
+    cc.k = -1;
+    bool done = false;
+#pragma unroll
+    for (int k = 0; k < PF; ++k) {
+        if (done || k >= npairs) break;
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {
+            if (done) break;
+            const float f = h ? dp[k].z : dp[k].x, b = h ? dp[k].w : dp[k].y;
+            if (b < d_in) continue;
+            if (f > d_out) {
+                done = true;
+                break;
+            }
+            const float sa = (f > d_in) ? fminf(fmaxf((f - g.z0) * g.idz, 0.f), 1.f) : 0.f;
+            const float sb = (b < d_out) ? fminf(fmaxf((b - g.z0) * g.idz, 0.f), 1.f) : 1.f;
+            if (sb > sa) {
+                if (FMT == 1) {
+                    cc.k = k;
+                    cc.q = cq[k];
+                }
+                const float4 col = get_colour<FMT>(cc, v, li, 2 * k + h);
+                const float da = fmaf(sa, g.dw, g.w1), db = fmaf(sb, g.dw, g.w1);
+                add_piece(acc, col, g.lw * (sb - sa) * rcp_fast(da * db));
+                ++n_segs;
+                if (ERT && acc.T <= kErtT) return;
+            }
+            if (b > d_out) done = true;
+        }
+    }
+    if (done) return;
+    PairCache pc;
+    pc.k = -1;
+    for (int j = 2 * PF; j < v.nsp; ++j) {
+        float f, b;
+        fetch_colour_pair<FMT>(cc, v, li, j >> 1);
+        get_fb(pc, v, li, j, f, b);
+        if (b < d_in) continue;
+        if (f > d_out) break;
+        const float sa = (f > d_in) ? fminf(fmaxf((f - g.z0) * g.idz, 0.f), 1.f) : 0.f;
+        const float sb = (b < d_out) ? fminf(fmaxf((b - g.z0) * g.idz, 0.f), 1.f) : 1.f;
+        if (sb > sa) {
+            const float4 col = get_colour<FMT>(cc, v, li, j);
+            const float da = fmaf(sa, g.dw, g.w1), db = fmaf(sb, g.dw, g.w1);
+            add_piece(acc, col, g.lw * (sb - sa) * rcp_fast(da * db));
+            ++n_segs;
+            if (ERT && acc.T <= kErtT) return;
+        }
+        if (b > d_out) break;
+    }
+}
+
+// ---------------------------------------------------------------------------
 // Exact path with empty-space skipping (Section 4.3): an outer walk over the
 // cells of the count grid (T x T lists by slabs of equal V_O view depth)
 // jumps over every cell whose count is 0 -- no supersegment overlaps it, so

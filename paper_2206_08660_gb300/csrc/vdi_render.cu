@@ -19,7 +19,8 @@ namespace vdi {
 // PATH: 0 = exact walk over every list (the default), 1 = exact walk with
 // empty-space skipping over the count grid, 2 = ray-subsampled preview
 // (D_R > 1), 3 = exact walk with range-block skipping, 4 = ray-subsampled
-// preview with a wide supersegment probe (for launches with few rays).
+// preview with a wide supersegment probe (for launches with few rays), 5 =
+// exact path for a view from V_O's eye (one list per ray).
 template <int FMT, int MODE, bool ERT, int WX, int PATH>
 __global__ void __launch_bounds__(256) render_kernel(const ViewConsts c, const DevVdi v, void *out,
                                                      int out_fmt, uint32_t *ray_lists,
@@ -40,6 +41,8 @@ __global__ void __launch_bounds__(256) render_kernel(const ViewConsts c, const D
             march_exact_ess<FMT, MODE, ERT>(v, r, acc, nl, nsg);
         else if (PATH == 3)
             march_exact<FMT, MODE, ERT, false, true>(v, r, acc, nl, nsg);
+        else if (PATH == 5)
+            march_single<FMT, MODE, ERT>(v, r, acc, nl, nsg);
         else if (r.dz >= 0.f)  // two copies of the walk, one per depth direction
             march_exact<FMT, MODE, ERT, false, false, 1>(v, r, acc, nl, nsg);
         else
@@ -153,6 +156,8 @@ static cudaError_t launch_m(const ViewConsts &c, const DevVdi &v, void *out, int
     if (!ert) return launch_ws<FMT, MODE, false, 0>(c, v, out, out_fmt, rl, rs, warp_shape, st);
     if (rl || rs) return launch_ws<FMT, MODE, true, 0>(c, v, out, out_fmt, rl, rs, warp_shape, st);
     if (ess) return launch_ws<FMT, MODE, true, 1>(c, v, out, out_fmt, rl, rs, warp_shape, st);
+    if (!blocks && c.single_list && MODE == kSearchAlg2)
+        return launch_ws<FMT, MODE, true, 5>(c, v, out, out_fmt, rl, rs, warp_shape, st);
     if (!blocks) return launch_ws<FMT, MODE, true, 0>(c, v, out, out_fmt, rl, rs, warp_shape, st);
     return launch_ws<FMT, MODE, true, 3>(c, v, out, out_fmt, rl, rs, warp_shape, st);
 }

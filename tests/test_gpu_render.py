@@ -298,3 +298,26 @@ def test_tiny_and_thin_images(V, ctx, orc, W, H):
         check_tolerance(gpu_render(V, vdi, cn, W, H), ref, 1, mask=fl == 0, what=f"{W}x{H}")
     finally:
         V.vdi_destroy(vdi)
+
+
+@pytest.mark.parametrize("fmt", [0, 1])
+@pytest.mark.parametrize("zoom", [1.0, 1.4])
+def test_views_from_the_original_eye(V, ctx, orc, fmt, zoom):
+    """A new view from V_O's eye (any field of view) takes the one-list-per-ray
+    path: its image is bit-identical to the general list walk (the counter
+    kernel runs the walk) and matches the oracle."""
+    case = random_case(40, 30, 9, seed=17, u=0.15, alpha_range=(0.05, 0.8), fill=0.9)
+    sc = case.oracle_scene(orc)
+    vdi = V.vdi_create(ctx, case.gpu_desc(V, fmt), case.vdi.rgba, case.vdi.depth, case.vdi.counts)
+    try:
+        W, H = 83, 61
+        cn = S.orbit_camera(case.bmin, case.bmax, W / H, az_deg=0.0, el_deg=15.0, zoom=zoom)
+        np.testing.assert_allclose(cn.eye, case.cam_o.eye)
+        fast = gpu_render(V, vdi, cn, W, H)
+        walk, _, _ = gpu_render(V, vdi, cn, W, H, counters=True)
+        assert np.array_equal(fast, walk)
+        ref, _, _, fl = orc.render_exact(sc, cn.view, cn.proj, W, H)
+        assert ref[:, 3].max() > 0.3
+        check_tolerance(fast, ref, fmt, mask=fl == 0, what=f"eye view zoom {zoom}")
+    finally:
+        V.vdi_destroy(vdi)
