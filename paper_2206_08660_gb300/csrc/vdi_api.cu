@@ -327,6 +327,20 @@ vdi_status make_view_consts(const vdi_t *v, const vdi_camera *cam, int W, int H,
             c->ry1 = (int)fmin(ceil(yhi) + 1.0, (double)H);
         }
     }
+    // the render grid's tiles that meet the rectangle (clamped to the image)
+    c->tiles_x = (W + 31) / 32;
+    {
+        const int x0 = max(c->rx0, 0), x1 = min(c->rx1, W - 1);
+        const int y0 = max(c->ry0, 0), y1 = min(c->ry1, H - 1);
+        if (x0 <= x1 && y0 <= y1) {
+            c->tile_x0 = x0 / 32;
+            c->tile_y0 = y0 / 8;
+            c->tile_w = x1 / 32 - c->tile_x0 + 1;
+            c->tile_h = y1 / 8 - c->tile_y0 + 1;
+        } else {
+            c->tile_x0 = c->tile_y0 = c->tile_w = c->tile_h = 0;
+        }
+    }
     c->sx = (float)(2.0 / W);
     c->sy = (float)(2.0 / H);
     c->d_r = d_r;
@@ -629,7 +643,7 @@ VDI_API vdi_status vdi_render_ex(vdi_t *v, const vdi_camera *view, int W, int H,
     ViewConsts c;
     st_ = make_view_consts(v, view, Wr, Hr, d_r, &c);
     if (st_ != VDI_OK) return st_;
-    const int ws = o.warp_shape >= 0 ? o.warp_shape : default_warp_shape(v, Wr, Hr);
+    const int ws = o.warp_shape >= 0 ? o.warp_shape : default_warp_shape(c);
     float4 *lo = nullptr;
     if (d_i == 1) {
         CK(launch_render(c, v->dv, out_rgba, out_fmt, o.ray_lists, o.ray_segs, o.search, ws, !o.no_ert, o.ess != 0, o.blocks != 0, st));
@@ -653,7 +667,7 @@ VDI_API vdi_status vdi_render_scaled(vdi_t *v, const vdi_camera *view, int W, in
     ViewConsts c;
     st_ = make_view_consts(v, view, Wr, Hr, d_r, &c);
     if (st_ != VDI_OK) return st_;
-    const int ws = default_warp_shape(v, Wr, Hr);
+    const int ws = default_warp_shape(c);
     float4 *lo = nullptr;
     if (Wr == W && Hr == H) {
         CK(launch_render(c, v->dv, out_rgba, out_fmt, nullptr, nullptr, VDI_SEARCH_ALG2, ws, true, false, false, st));

@@ -44,9 +44,11 @@ vdi_status check_render_args(const vdi_t *v, int W, int H, int d_i, int d_r, con
 void release_batch_cache(vdi_ctx *ctx);
 cudaError_t launch_block_range(const DevVdi &v, float2 *brange, cudaStream_t st);
 
-// warp shape used when the caller does not choose one: 32x1 (lanes along a
-// row of lists) unless the autotuner recorded a better one
-inline int default_warp_shape(const vdi_t *, int, int) { return 3; }  // 4 x 8 pixels per warp
+// warp shape used when the caller does not choose one: 4 x 8 pixels per warp
+// (lanes whose rays cross neighbouring lists together), except for exact
+// renders from V_O's eye, where each lane reads one list and 32 x 1 pixels
+// per warp read 32 neighbouring lists' records at once
+inline int default_warp_shape(const vdi::ViewConsts &c) { return (c.single_list && c.d_r == 1) ? 0 : 3; }
 
 // rays a request renders: explicit (Wr, Hr) when given, else ceil(W / d_i) x ceil(H / d_i)
 template <class R>

@@ -72,6 +72,10 @@ struct ViewConsts {
     float inv_u;        // 1 / length_unit
     int W, H;           // rays rendered (after D_I)
     int rx0, rx1, ry0, ry1;  // pixel rectangle holding the box's image; rays outside it miss the box
+    // 32 x 8 tiles of the render grid: tiles_x per row; the tiles meeting the
+    // rectangle above span [tile_x0, tile_x0 + tile_w) x [tile_y0, tile_y0 + tile_h)
+    // (tile_w = tile_h = 0 when it is empty)
+    int tiles_x, tile_x0, tile_y0, tile_w, tile_h;
     float sx, sy;       // 2/W, 2/H
     int d_r;            // ray subsampling (1 = exact path)
     float cell_scale;   // length_unit / (slab view-depth extent * d_r)

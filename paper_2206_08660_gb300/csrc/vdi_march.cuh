@@ -411,15 +411,17 @@ __device__ __forceinline__ void march_exact(const DevVdi &v, Ray &r, Accum &acc,
 // Views from V_O's own eye (Section 4.1 at zero deviation): every ray projects
 // to one point of V_O's image plane and stays in one list.  A ray that the
 // list walk would treat as exactly one list over s in [0, 1] is composited
-// here with the list's first PF slot pairs (depth and colour records)
-// requested at once, instead of one dependent round trip per pair; its
-// arithmetic is process_list's, so the image is the same.  Any other ray
-// takes the list walk.
+// here with the list's slot pairs (depth and colour records) requested PF at
+// a time, instead of one dependent round trip per pair; its arithmetic is
+// process_list's, so the image is the same.  Any other ray takes the list
+// walk.
 // ---------------------------------------------------------------------------
+constexpr int kSinglePF = 4;  // slot pairs march_single requests at once
+
 template <int FMT, int MODE, bool ERT>
 __device__ __forceinline__ void march_single(const DevVdi &v, Ray &r, Accum &acc, uint32_t &n_lists,
                                              uint32_t &n_segs) {
-    constexpr int PF = 4;
+    constexpr int PF = kSinglePF;
     const int ox = r.ox, oy = r.oy;
     const float dgx = r.dgx, dgy = r.dgy;
     const int ix = min(max(ox, 0), v.w - 1), iy = min(max(oy, 0), v.h - 1);
@@ -448,57 +450,50 @@ __device__ __forceinline__ void march_single(const DevVdi &v, Ray &r, Accum &acc
             if (FMT == 1) cq[k] = __ldg(reinterpret_cast<const uint4 *>(v.colour) + (k * v.nl32 + li));
         }
     if (d_out < rg.x || d_in > rg.y) return;
-    // slots in order; those with b < d_in lie before the first one met (b is sorted)
+    // slots in order; those with b < d_in lie before the first one met (b is
+    // sorted).  The records come PF slot pairs at a time: the next PF pairs are
+    // requested together once the current ones are used up.
     ColourCache<FMT> cc;
     cc.k = -1;
     bool done = false;
+    for (int k0 = 0; k0 < npairs; k0 += PF) {
+        if (k0 > 0) {
 #pragma unroll
-    for (int k = 0; k < PF; ++k) {
-        if (done || k >= npairs) break;
-#pragma unroll
-        for (int h = 0; h < 2; ++h) {
-            if (done) break;
-            const float f = h ? dp[k].z : dp[k].x, b = h ? dp[k].w : dp[k].y;
-            if (b < d_in) continue;
-            if (f > d_out) {
-                done = true;
-                break;
-            }
-            const float sa = (f > d_in) ? fminf(fmaxf((f - g.z0) * g.idz, 0.f), 1.f) : 0.f;
-            const float sb = (b < d_out) ? fminf(fmaxf((b - g.z0) * g.idz, 0.f), 1.f) : 1.f;
-            if (sb > sa) {
-                if (FMT == 1) {
-                    cc.k = k;
-                    cc.q = cq[k];
+            for (int k = 0; k < PF; ++k)
+                if (k0 + k < npairs) {
+                    dp[k] = ld_depth_pair(v, k0 + k, li);
+                    if (FMT == 1) cq[k] = __ldg(reinterpret_cast<const uint4 *>(v.colour) + ((k0 + k) * v.nl32 + li));
                 }
-                const float4 col = get_colour<FMT>(cc, v, li, 2 * k + h);
-                const float da = fmaf(sa, g.dw, g.w1), db = fmaf(sb, g.dw, g.w1);
-                add_piece(acc, col, g.lw * (sb - sa) * rcp_fast(da * db));
-                ++n_segs;
-                if (ERT && acc.T <= kErtT) return;
+        }
+#pragma unroll
+        for (int k = 0; k < PF; ++k) {
+            if (done || k0 + k >= npairs) break;
+#pragma unroll
+            for (int h = 0; h < 2; ++h) {
+                if (done) break;
+                const float f = h ? dp[k].z : dp[k].x, b = h ? dp[k].w : dp[k].y;
+                if (b < d_in) continue;
+                if (f > d_out) {
+                    done = true;
+                    break;
+                }
+                const float sa = (f > d_in) ? fminf(fmaxf((f - g.z0) * g.idz, 0.f), 1.f) : 0.f;
+                const float sb = (b < d_out) ? fminf(fmaxf((b - g.z0) * g.idz, 0.f), 1.f) : 1.f;
+                if (sb > sa) {
+                    if (FMT == 1) {
+                        cc.k = k0 + k;
+                        cc.q = cq[k];
+                    }
+                    const float4 col = get_colour<FMT>(cc, v, li, 2 * (k0 + k) + h);
+                    const float da = fmaf(sa, g.dw, g.w1), db = fmaf(sb, g.dw, g.w1);
+                    add_piece(acc, col, g.lw * (sb - sa) * rcp_fast(da * db));
+                    ++n_segs;
+                    if (ERT && acc.T <= kErtT) return;
+                }
+                if (b > d_out) done = true;
             }
-            if (b > d_out) done = true;
         }
-    }
-    if (done) return;
-    PairCache pc;
-    pc.k = -1;
-    for (int j = 2 * PF; j < v.nsp; ++j) {
-        float f, b;
-        fetch_colour_pair<FMT>(cc, v, li, j >> 1);
-        get_fb(pc, v, li, j, f, b);
-        if (b < d_in) continue;
-        if (f > d_out) break;
-        const float sa = (f > d_in) ? fminf(fmaxf((f - g.z0) * g.idz, 0.f), 1.f) : 0.f;
-        const float sb = (b < d_out) ? fminf(fmaxf((b - g.z0) * g.idz, 0.f), 1.f) : 1.f;
-        if (sb > sa) {
-            const float4 col = get_colour<FMT>(cc, v, li, j);
-            const float da = fmaf(sa, g.dw, g.w1), db = fmaf(sb, g.dw, g.w1);
-            add_piece(acc, col, g.lw * (sb - sa) * rcp_fast(da * db));
-            ++n_segs;
-            if (ERT && acc.T <= kErtT) return;
-        }
-        if (b > d_out) break;
+        if (done) return;
     }
 }
 
@@ -751,6 +746,39 @@ __device__ __forceinline__ void tile_offset(int &dx, int &dy) {
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     dx = (warp % BWX) * WX + (lane % WX);
     dy = (warp / BWX) * WY + (lane / WX);
+}
+
+// The 32 x 8 tile of a linear block index: the tiles meeting the box's pixel
+// rectangle come first (row by row), so the blocks that walk the VDI are
+// dispatched together and fill the SMs; the tiles outside it (rays that miss
+// the box: transparent pixels) follow in row order.
+__device__ __forceinline__ void tile_of_block(const ViewConsts &c, int b, int &tx, int &ty) {
+    const int nrect = c.tile_w * c.tile_h;
+    if (b < nrect) {
+        const int r = b / c.tile_w;
+        ty = c.tile_y0 + r;
+        tx = c.tile_x0 + (b - r * c.tile_w);
+        return;
+    }
+    int k = b - nrect;
+    const int above = c.tile_y0 * c.tiles_x;  // whole rows above the rectangle
+    if (k < above) {
+        ty = k / c.tiles_x;
+        tx = k - ty * c.tiles_x;
+        return;
+    }
+    k -= above;
+    const int side = c.tiles_x - c.tile_w;  // tiles left and right of it in each of its rows
+    if (k < c.tile_h * side) {
+        const int r = k / side, q = k - r * side;
+        ty = c.tile_y0 + r;
+        tx = (q < c.tile_x0) ? q : q + c.tile_w;
+        return;
+    }
+    k -= c.tile_h * side;  // whole rows below it
+    const int r = k / c.tiles_x;
+    ty = c.tile_y0 + c.tile_h + r;
+    tx = k - r * c.tiles_x;
 }
 
 __device__ __forceinline__ void store_px(void *out, int out_fmt, size_t idx, const Accum &acc) {

@@ -69,7 +69,7 @@ VDI_API vdi_status vdi_render_preview_static(vdi_t *v, const vdi_camera *view, i
     ViewConsts c;
     st_ = make_view_consts(v, view, Wr, Hr, d_r, &c);
     if (st_ != VDI_OK) return st_;
-    const int ws = default_warp_shape(v, Wr, Hr);
+    const int ws = default_warp_shape(c);
     cudaError_t e;
     if (d_i == 1) {
         e = launch_render(c, v->dv, out_rgba, out_fmt, nullptr, nullptr, VDI_SEARCH_ALG2, ws, true, false, false, st);

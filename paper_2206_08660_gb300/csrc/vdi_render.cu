@@ -2,10 +2,12 @@
 // (Section 4), the subsampled previews (Section 4.4), upsampling, the
 // instrumented bytes-touched render and the search diagnostic.
 //
-// One thread per pixel ray.  A block covers 32 x 8 pixels; its eight warps
-// cover 32x1, 16x2, 8x4 or 4x8 pixels each (the warp shape is a launch choice:
-// lanes on neighbouring pixels walk neighbouring lists, so their 16-byte
-// depth/colour loads coalesce).
+// One thread per pixel ray.  A block covers a 32 x 8 tile that meets the
+// volume box's pixel rectangle (those blocks are dispatched first); its eight
+// warps cover 32x1, 16x2, 8x4 or 4x8 pixels each (the warp shape is a launch
+// choice: lanes on neighbouring pixels walk neighbouring lists, so their
+// 16-byte depth/colour loads coalesce).  The tiles outside the rectangle, whose
+// rays all miss the box, are cleared by the last blocks, several tiles each.
 #include <cuda_fp16.h>
 #include <cuda_runtime.h>
 #include <math.h>
@@ -21,13 +23,36 @@ namespace vdi {
 // (D_R > 1), 3 = exact walk with range-block skipping, 4 = ray-subsampled
 // preview with a wide supersegment probe (for launches with few rays), 5 =
 // exact path for a view from V_O's eye (one list per ray).
+constexpr int kFillTiles = 8;  // tiles outside the box's pixel rectangle per block
+
 template <int FMT, int MODE, bool ERT, int WX, int PATH>
 __global__ void __launch_bounds__(256) render_kernel(const ViewConsts c, const DevVdi v, void *out,
                                                      int out_fmt, uint32_t *ray_lists,
                                                      uint32_t *ray_segs) {
-    int lx, ly;
+    const int nrect = c.tile_w * c.tile_h;
+    if ((int)blockIdx.x >= nrect) {
+        // kFillTiles tiles outside the box's pixel rectangle: every ray misses
+        // the box, so the pixels are transparent and the counters zero
+        const int ntiles = c.tiles_x * ((c.H + 7) >> 3);
+        const int t0 = nrect + ((int)blockIdx.x - nrect) * kFillTiles, t1 = min(t0 + kFillTiles, ntiles);
+        const Accum miss = {0.f, 0.f, 0.f, 1.f};
+        for (int t = t0; t < t1; ++t) {
+            int tx, ty;
+            tile_of_block(c, t, tx, ty);
+            const int px = tx * 32 + (threadIdx.x & 31), py = ty * 8 + (threadIdx.x >> 5);
+            if (px < c.W && py < c.H) {
+                const size_t idx = (size_t)py * c.W + px;
+                store_px(out, out_fmt, idx, miss);
+                if (ray_lists) ray_lists[idx] = 0;
+                if (ray_segs) ray_segs[idx] = 0;
+            }
+        }
+        return;
+    }
+    int lx, ly, tx, ty;
     tile_offset<WX>(lx, ly);
-    const int px = blockIdx.x * 32 + lx, py = blockIdx.y * 8 + ly;
+    tile_of_block(c, blockIdx.x, tx, ty);
+    const int px = tx * 32 + lx, py = ty * 8 + ly;
     if (px >= c.W || py >= c.H) return;
     Accum acc = {0.f, 0.f, 0.f, 1.f};
     uint32_t nl = 0, nsg = 0;
@@ -129,7 +154,10 @@ __global__ void search_kernel(const DevVdi v, int li, const float *d_entry, cons
 template <int FMT, int MODE, bool ERT, int PATH>
 static cudaError_t launch_ws(const ViewConsts &c, const DevVdi &v, void *out, int out_fmt, uint32_t *rl,
                              uint32_t *rs, int warp_shape, cudaStream_t st) {
-    dim3 grid(div_up(c.W, 32), div_up(c.H, 8)), block(256);
+    // one block per 32 x 8 tile meeting the box's pixel rectangle, then one per
+    // kFillTiles tiles outside it (tile_of_block's order)
+    const int nrect = c.tile_w * c.tile_h, ntiles = div_up(c.W, 32) * div_up(c.H, 8);
+    dim3 grid(nrect + div_up(ntiles - nrect, kFillTiles)), block(256);
     // the ablation searches are built with the default warp shape (4 x 8) only
     if (MODE == kSearchAlg2 && warp_shape == 0)
         render_kernel<FMT, MODE, ERT, 32, PATH><<<grid, block, 0, st>>>(c, v, out, out_fmt, rl, rs);

@@ -301,7 +301,7 @@ def test_tiny_and_thin_images(V, ctx, orc, W, H):
 
 
 @pytest.mark.parametrize("fmt", [0, 1])
-@pytest.mark.parametrize("zoom", [1.0, 1.4])
+@pytest.mark.parametrize("zoom", [0.3, 1.0, 1.4])
 def test_views_from_the_original_eye(V, ctx, orc, fmt, zoom):
     """A new view from V_O's eye (any field of view) takes the one-list-per-ray
     path: its image is bit-identical to the general list walk (the counter
@@ -319,5 +319,49 @@ def test_views_from_the_original_eye(V, ctx, orc, fmt, zoom):
         ref, _, _, fl = orc.render_exact(sc, cn.view, cn.proj, W, H)
         assert ref[:, 3].max() > 0.3
         check_tolerance(fast, ref, fmt, mask=fl == 0, what=f"eye view zoom {zoom}")
+    finally:
+        V.vdi_destroy(vdi)
+
+
+@pytest.mark.parametrize("zoom,shift", [(0.35, 0.0), (1.0, 0.45), (0.35, 3.0)])
+def test_tiles_outside_the_box_image(V, ctx, orc, zoom, shift):
+    """The render grid dispatches the tiles that meet the box's pixel
+    rectangle first and clears the others in blocks of several tiles: with the
+    box small on screen, cut by the image's left and bottom edges, or out of
+    the view entirely (look-at point moved sideways by shift times the eye's
+    distance), every pixel and both per-ray counters still match the oracle;
+    the cleared pixels are transparent and their counters zero."""
+    case = random_case(31, 19, 4, seed=21, u=0.2, alpha_range=(0.05, 0.8))
+    sc = case.oracle_scene(orc)
+    vdi = V.vdi_create(ctx, case.gpu_desc(V, 1), case.vdi.rgba, case.vdi.depth, case.vdi.counts)
+    try:
+        W, H = 203, 91  # 7 x 12 tiles with ragged edges
+        cn = S.orbit_camera(case.bmin, case.bmax, W / H, az_deg=12.0, el_deg=10.0, zoom=zoom)
+        if shift:
+            centre = 0.5 * (np.asarray(case.bmin) + np.asarray(case.bmax))
+            side = np.cross(centre - cn.eye, (0.0, 1.0, 0.0))
+            side *= np.linalg.norm(centre - cn.eye) / np.linalg.norm(side)
+            cn = S.Camera(S.look_at(cn.eye, centre + shift * side), cn.proj, cn.eye)
+        ref, lists, segs, fl = orc.render_exact(sc, cn.view, cn.proj, W, H)
+        out = torch.full((H, W, 4), 7.0, dtype=torch.float32, device="cuda")
+        rl = torch.full((H, W), 99, dtype=torch.int32, device="cuda")
+        rs = torch.full((H, W), 99, dtype=torch.int32, device="cuda")
+        V.vdi_render_ex(vdi, V.camera(cn.view, cn.proj), W, H, 1, 1, out, V.VDI_F32, ray_lists=rl, ray_segs=rs)
+        fast = torch.full((H, W, 4), 7.0, dtype=torch.float32, device="cuda")
+        V.vdi_render(vdi, V.camera(cn.view, cn.proj), W, H, 1, 1, fast, V.VDI_F32)
+        torch.cuda.synchronize()
+        got = out.cpu().numpy().reshape(-1, 4)
+        assert np.array_equal(got, fast.cpu().numpy().reshape(-1, 4))
+        ok = fl == 0
+        check_tolerance(got, ref, 1, mask=ok, what=f"shift {shift}")
+        assert np.array_equal(rl.cpu().numpy().reshape(-1)[ok], lists[ok])
+        assert np.array_equal(rs.cpu().numpy().reshape(-1)[ok], segs[ok])
+        seen = ref[:, 3].reshape(H, W) > 0
+        if shift == 0.0:
+            assert 0.01 < seen.mean() < 0.1, seen.mean()  # small on screen: most tiles are cleared
+        elif shift < 1.0:
+            assert seen[:, 0].any() and seen[-1, :].any() and seen.mean() < 0.4  # cut by two image edges
+        else:
+            assert not seen.any() and np.all(got == 0)
     finally:
         V.vdi_destroy(vdi)
