@@ -302,11 +302,14 @@ def test_tiny_and_thin_images(V, ctx, orc, W, H):
 
 @pytest.mark.parametrize("fmt", [0, 1])
 @pytest.mark.parametrize("zoom", [0.3, 1.0, 1.4])
-def test_views_from_the_original_eye(V, ctx, orc, fmt, zoom):
+@pytest.mark.parametrize("ns", [9, 20])
+def test_views_from_the_original_eye(V, ctx, orc, fmt, zoom, ns):
     """A new view from V_O's eye (any field of view) takes the one-list-per-ray
     path: its image is bit-identical to the general list walk (the counter
-    kernel runs the walk) and matches the oracle."""
-    case = random_case(40, 30, 9, seed=17, u=0.15, alpha_range=(0.05, 0.8), fill=0.9)
+    kernel runs the walk) and matches the oracle.  N_S = 9 and 20 with lists
+    of every fill give odd and even supersegment counts and one to three
+    batches of slot pairs."""
+    case = random_case(40, 30, ns, seed=17, u=0.15, alpha_range=(0.05, 0.8), fill=0.9)
     sc = case.oracle_scene(orc)
     vdi = V.vdi_create(ctx, case.gpu_desc(V, fmt), case.vdi.rgba, case.vdi.depth, case.vdi.counts)
     try:
