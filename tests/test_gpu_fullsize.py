@@ -3,7 +3,8 @@ times, over whole images.
 
 * large: 1024^3 uint8 mixing layer -> GPU vdi_generate 1920x1080, N_S = 20,
   FP16 colour; renders at 10 and 30 degrees and the previews (D_I, D_R) =
-  (2, 2), (4, 4) at 30 degrees, all 1920x1080 (the benchmark step).
+  (2, 2), (4, 4) at 30 degrees, all 1920x1080 (the benchmark step), and the
+  0- and 5-degree views of the near-view roofline measurement.
 * plain: 256^3 uint16 value noise -> 1280x720, N_S = 20, tau = 0.01, FP32;
   views 0/5/15/30 degrees, zoom 1.2.
 * batched: 4 resident VDIs (640x360 N_S=8, 1280x720 N_S=16, 1920x1080 N_S=20,
@@ -82,7 +83,11 @@ def test_large_workload_benchmark_frames(V, ctx, orc):
     cam_o, views = B.cameras(wl, bmin, bmax)
     vdi, sc, _, _ = both(V, ctx, orc, wl, vol, cam_o)
     try:
-        for (az, d_i, d_r), cn in zip(wl["frames"], views):
+        # the benchmark step's frames, and the near views of its roofline entry (0 degrees
+        # is a view from V_O's eye: the one-list-per-ray path)
+        near = [((az, 1, 1), S.orbit_camera(bmin, bmax, wl["W"] / wl["H"], az_deg=az, el_deg=wl["el"],
+                                            zoom=wl["zoom"])) for az in (0.0, 5.0)]
+        for (az, d_i, d_r), cn in list(zip(wl["frames"], views)) + near:
             if az == 20.0:
                 continue  # 10 and 30 degrees bracket it; keeps the test short
             got = gpu_frame(V, vdi, cn, wl["W"], wl["H"], d_i, d_r)
