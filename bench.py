@@ -722,7 +722,9 @@ def main():
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                      "frac": achieved / peak, "traffic": traffic, "peak_source": peak_src,
                      "kernel": "render_kernel (exact path)",
-                     "algorithmic_bytes_per_launch": [int(b) for b in touched]},
+                     "algorithmic_bytes_per_launch": [int(b) for b in touched],
+                     "frac_per_frame": {f"{wl['frames'][i][0]:g}deg": float(tb / (ms / 1e3) / 1e9 / peak)
+                                        for i, tb, ms in zip(exact, touched, exact_ms)}},
         "clocks": clocks, "e2e": e2e, "gpu_launches": launches_per_step * args.steps, "ablation": ablation,
         "roofline_near_original_view": near, "batched_step": batched_step,
         "vdi_generate_ms": gen_s * 1e3, "generation": generation, "quality": quality, "preview_control": control, "vdi_bytes": int(layout.depth_bytes + layout.colour_bytes),
