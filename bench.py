@@ -240,8 +240,11 @@ class OracleLeg:
         return int(min(200000, max(probe, probe * budget_s / max(m, 1e-6))))
 
     def sample_text(self, R):
-        return (f"{R} random rays from each of the {len(self.wl['frames'])} frames per step, timed and extrapolated "
-                f"to full frames; oracle VDI from the oracle's own FP32 generation")
+        counts = sorted({min(R, (-(-self.wl["W"] // d_i)) * (-(-self.wl["H"] // d_i)))
+                         for (_, d_i, _) in self.wl["frames"]})
+        n = str(counts[0]) if len(counts) == 1 else "/".join(str(c) for c in counts)
+        return (f"{n} random rays (drawn with repetition) from each of the {len(self.wl['frames'])} frames per step, "
+                f"timed and extrapolated to full frames; oracle VDI from the oracle's own FP32 generation")
 
 
 SERVING = dict(n_vdis=8, w=1920, h=1080, ns=24, tau=0.01, vol_n=512, rate=240.0, seconds=8.0, replace_every=2.0,
