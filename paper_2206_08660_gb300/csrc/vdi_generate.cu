@@ -268,13 +268,15 @@ __device__ int gen_march(const GenConsts &g, const GenRay &r, float tau, float4 
 // supersegments, delta = floor(0.15 N_S).  The search starts at 1e-5 and
 // keeps it if that gives fewer than N_S; more than N_S raises the lower end,
 // fewer than N_S - delta lowers the upper end; an interval narrower than
-// 1e-4 ends the search with the upper end (the side that does not exceed
-// N_S).  FP32 with explicit rounding, like the march, so every ray's gamma is
-// reproducible.
+// 1e-6 (the supplement's value) ends the search with the upper end (the side
+// that does not exceed N_S).  In [0, sqrt(3)] an FP32 ulp is at most 1.2e-7,
+// so every interval still to be halved holds more than eight ulps and its
+// midpoint lies strictly inside it.  FP32 with explicit rounding, like the
+// march, so every ray's gamma is reproducible.
 __device__ float adaptive_tau(const GenConsts &g, const GenRay &r) {
     const int delta = (15 * g.ns) / 100;
     float low = 0.f, high = (float)1.7320508075688772, gamma = (float)1e-5;
-    const float eps = (float)1e-4;
+    const float eps = (float)1e-6;
     bool first = true, found = false;
     float ff = 0.f, lb = 0.f;
     while (!found) {
