@@ -485,7 +485,8 @@ def main():
         ms = 1e3 * float(np.mean(t_all))
         val = frames_per_step / (ms / 1e3)
         cores, sample = leg.threads, leg.sample_text(R)
-        print(json.dumps({"impl": "reference", "metric": METRIC, "value": val, "unit": "frames/s", "n_gpus": 1,
+        print(json.dumps({"impl": "reference", "metric": METRIC, "value": val, "unit": "frames/s", "n_gpus": world,
+                          "note": "the FP64 oracle on rank 0's host cores; the other ranks do no work",
                           "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
                           "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
                           "config": config,

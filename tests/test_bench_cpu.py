@@ -24,3 +24,21 @@ def test_reference_arm_prints_one_json_line():
     e = d["e2e"]
     assert e["value"] == d["value"] and e["unit"] == d["unit"]
     assert e["h2d_bytes_per_step"] == 0 and e["d2h_bytes_per_step"] == 0
+
+
+def test_reference_arm_under_two_ranks_prints_once():
+    """Launched like the multi-GPU benchmark (torchrun, two ranks, rendezvous on
+    127.0.0.1): rank 0 alone runs the oracle and prints the line; the other rank
+    exits 0 without work."""
+    import random
+
+    port = str(random.randint(29600, 29999))
+    r = subprocess.run([sys.executable, "-m", "torch.distributed.run", "--nnodes=1", "--nproc-per-node", "2",
+                        "--master-addr", "127.0.0.1", "--master-port", port, os.path.join(ROOT, "bench.py"),
+                        "--impl", "reference", "--workload", "tiny", "--steps", "1", "--warmup", "1", "--gpus", "2"],
+                       capture_output=True, text=True, timeout=600, cwd=ROOT)
+    assert r.returncode == 0, r.stderr[-2000:]
+    lines = [ln for ln in r.stdout.splitlines() if ln.strip().startswith("{")]
+    assert len(lines) == 1
+    d = json.loads(lines[0])
+    assert d["impl"] == "reference" and d["n_gpus"] == 2 and d["value"] > 0
