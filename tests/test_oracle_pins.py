@@ -345,3 +345,215 @@ def test_ray_subsampled_preview_exact_on_slab_with_faces_on_edges(orc, d_r):
     # every occupied cell lies inside the slab, so equal spacing composes to the exact length
     assert np.abs(pv - ex).max() < 1e-9
     assert ex[:, 3].max() > 0.1
+
+
+# ---------------------------------------------------------------- D_R sample count (Section 4.4): an image that depends on n
+
+
+def _stack_in_slab(w, h, ns, co, e, k0, d_r_pattern=None):
+    """Every list holds supersegments inside grid slab k0 only (view-depth
+    fractions of the slab): S1 = [0.02, 0.60]; lists with even ix also hold
+    three thin ones, [0.70, 0.72], [0.80, 0.82], [0.90, 0.92].  Returns the VDI
+    and, per list parity, the supersegments' view-depth ranges and (chat, alpha)."""
+    dk, dk1 = view_depth(co, float(e[k0])), view_depth(co, float(e[k0 + 1]))
+    fr = [(0.02, 0.60), (0.70, 0.72), (0.80, 0.82), (0.90, 0.92)]
+    cols = [((0.9, 0.3, 0.1), 0.35), ((0.1, 0.8, 0.2), 0.5), ((0.2, 0.2, 0.9), 0.4), ((0.7, 0.7, 0.1), 0.6)]
+    v = S.VdiArrays(w, h, ns, np.zeros((h, w, ns, 4), np.float32), np.full((h, w, ns, 2), np.inf, np.float32),
+                    np.zeros((h, w), np.int32))
+    segs = {}
+    for parity, m in ((0, 4), (1, 1)):
+        rows = []
+        for j in range(m):
+            zf = np.float32(S.ndc_z_of_view_depth(co.proj, dk + fr[j][0] * (dk1 - dk)))
+            zb = np.float32(S.ndc_z_of_view_depth(co.proj, dk + fr[j][1] * (dk1 - dk)))
+            chat, a = np.asarray(cols[j][0], np.float32), np.float32(cols[j][1])
+            c32 = (chat * a).astype(np.float32)
+            v.depth[:, parity::2, j] = (zf, zb)
+            v.rgba[:, parity::2, j, :3] = c32
+            v.rgba[:, parity::2, j, 3] = a
+            # the field the VDI defines: chat = C / alpha of the stored FP32 values
+            rows.append((view_depth(co, float(zf)), view_depth(co, float(zb)),
+                         c32.astype(np.float64) / float(a), float(a)))
+        v.counts[:, parity::2] = m
+        segs[parity] = rows
+    return v, segs, (dk, dk1)
+
+
+@pytest.mark.parametrize("d_r", [1, 2])
+def test_ray_subsampled_preview_sample_count(orc, d_r):
+    """Rendered from V_O's own camera at the VDI's resolution, every ray runs down
+    its list's centre and crosses only slabs of the count grid.  The one occupied
+    slab holds c supersegments over the cell's F lists; the preview places
+    n = ceil((c / F) (l_c / slab depth extent) / D_R) samples at the midpoints of n
+    equal pieces of the ray's chord through the slab, and each takes the colour
+    of the supersegment containing it with opacity for the spacing l_c / n.
+    Expected values come from camera-basis rays, Cyrus-Beck box clipping and the
+    closed-form view depth of the stored faces; the supersegments are thinner
+    than the slab, so the image depends on n (planted floor-for-ceil, x D_R, and
+    T instead of the cell's list count each fail here)."""
+    w, h, T, nz, k0, u = 43, 30, 8, 10, 5, 0.03  # ragged last cell column (3 lists) and row (6 lists)
+    co = S.orbit_camera(BMIN, BMAX, w / h, el_deg=15, zoom=2.6)  # the box fills the view, ragged cells included
+    e = orc.grid_edges(scene(orc, S.random_vdi(w, h, 2, fill=0), co, u), nz)
+    vdi, segs, (dk, dk1) = _stack_in_slab(w, h, 4, co, e, k0)
+    sc = scene(orc, vdi, co, u)
+    got, fl = orc.render_preview(sc, co.view, co.proj, w, h, d_r, T, nz)
+
+    nN, fN = near_far(co)
+    dz_cell = (fN - nN) / nz
+    eye, dirs = cam_rays(co, w, h, fovy_of(co), w / h)
+    checked, ns_seen = 0, {}
+    for q in range(w * h):
+        ix, iy = q % w, q // w
+        s0, s1 = clip_interval(eye, dirs[q], box_planes(BMIN, BMAX), nN, fN)
+        sa, sb = max(s0, dk), min(s1, dk1)  # view depth along these rays
+        if not sb > sa:
+            assert np.all(got[q] == 0)
+            checked += 1
+            continue
+        L = np.linalg.norm(dirs[q])
+        lc = (sb - sa) * L
+        cx, cy = ix // T, iy // T
+        xs, ys = range(cx * T, min(cx * T + T, w)), range(cy * T, min(cy * T + T, h))
+        c = sum(len(segs[x % 2]) for x in xs) * len(ys)
+        want = (c / (len(xs) * len(ys))) * (lc / dz_cell) / d_r
+        if abs(want - round(want)) < 1e-7 * want:
+            continue  # a count at a rounding boundary
+        n = max(1, math.ceil(want))
+        acc = np.zeros(4)
+        tie = False
+        for i in range(n):
+            s = sa + (i + 0.5) * (sb - sa) / n
+            for (vf, vb, chat, a) in segs[ix % 2]:
+                if min(abs(s - vf), abs(s - vb)) < 1e-9:
+                    tie = True
+                if vf <= s <= vb:
+                    at = 1 - (1 - a) ** ((lc / n) / u)
+                    acc[:3] += (1 - acc[3]) * chat * at
+                    acc[3] += (1 - acc[3]) * at
+                    break
+        if tie:
+            continue
+        assert np.abs(got[q] - acc).max() < 1e-9, (q, n, got[q], acc)
+        checked += 1
+        ns_seen[n] = ns_seen.get(n, 0) + 1
+    assert checked > 0.95 * w * h
+    assert got.reshape(h, w, 4)[:, -1, 3].min() > 0 and got.reshape(h, w, 4)[-1, :, 3].min() > 0
+    assert len(ns_seen) >= 2 and sum(ns_seen.values()) > 200, ns_seen  # the image depends on n across the view
+    assert got[:, 3].max() > 0.3
+
+
+# ---------------------------------------------------------------- per-ray counters: lists crossed, pieces inside supersegments
+
+
+def pixel_rays(cam, W, H):
+    """Pixel-centre rays of a perspective or orthographic camera from its basis:
+    origins (n, 3) and directions (n, 3) with unit view-space depth, so
+    o + s d sits at view depth s (no matrix inverse)."""
+    px, py = np.meshgrid(np.arange(W), np.arange(H))
+    x = 2 * (px.ravel() + 0.5) / W - 1
+    y = 1 - 2 * (py.ravel() + 0.5) / H
+    R = cam.view[:3, :3]  # rows: right, up, -forward
+    P = cam.proj
+    if P[3, 3] == 1.0:  # orthographic: parallel rays from points of the view plane
+        o = cam.eye + (x / P[0, 0])[:, None] * R[0] + (y / P[1, 1])[:, None] * R[1]
+        d = np.repeat(-R[2][None, :], len(x), 0)
+        return o, d
+    th = 1.0 / P[1, 1]
+    dv = np.stack([x * th * (P[1, 1] / P[0, 0]), y * th, -np.ones_like(x)], 1)
+    return np.repeat(cam.eye[None, :], len(x), 0), dv @ R
+
+
+def lines_between(a, b, n):
+    """Interior grid lines k (1 <= k <= n - 1) strictly between grid coordinates a and b."""
+    lo, hi = min(a, b), max(a, b)
+    return [k for k in range(max(1, math.floor(lo) + 1), min(n - 1, math.ceil(hi) - 1) + 1) if lo < k < hi]
+
+
+@pytest.mark.parametrize("az,el,zoom,ortho", [(20.0, 10.0, 1.3, False), (-50.0, 30.0, 1.0, False),
+                                             (35.0, 15.0, 1.2, True), (125.0, -10.0, 1.4, False)])
+def test_ray_counters_match_lines_crossed(orc, az, el, zoom, ortho):
+    """A new-view ray is a straight segment in V_O's NDC, so the lists it passes
+    through with positive length number one more than the interior list-grid
+    lines between the NDC images of its clipped ends (Fig. 3), empty lists
+    included.  With a slab in every non-empty list, the pieces inside
+    supersegments are the lists crossed by the part of the ray between the two
+    slab planes.  Clip ends come from Cyrus-Beck against the box, V_O's frustum
+    planes and V_N's near/far range; rays with a tie (an end or a crossing
+    within 1e-9 list widths of a grid line) are skipped."""
+    w, h = 23, 17
+    co = S.orbit_camera(BMIN, BMAX, w / h, el_deg=10, zoom=2.0)  # V_O's frustum cuts the box
+    n0, f0 = near_far(co)
+    zf = np.float32(S.ndc_z_of_view_depth(co.proj, n0 + 0.4 * (f0 - n0)))
+    zb = np.float32(S.ndc_z_of_view_depth(co.proj, n0 + 0.55 * (f0 - n0)))
+    vdi = S.slab_vdi(w, h, 2, zf, zb, alpha=0.2)
+    empty = (np.add.outer(np.arange(h), np.arange(w)) % 3) == 0  # every third diagonal of lists is empty
+    vdi.depth[empty] = np.inf
+    vdi.rgba[empty] = 0
+    vdi.counts[empty] = 0
+    sc = scene(orc, vdi, co, 0.1)
+    W, H = 40, 30
+    cn = S.orbit_camera(BMIN, BMAX, W / H, az_deg=az, el_deg=el, zoom=zoom, ortho=ortho)
+    _, nl, nsg, _ = orc.render_exact(sc, cn.view, cn.proj, W, H)
+
+    M = co.proj @ co.view
+    planes = box_planes(BMIN, BMAX) + frustum_planes(M)
+    origins, dirs = pixel_rays(cn, W, H)
+    nN, fN = near_far(cn) if not ortho else ((cn.proj[2, 3] + 1) / cn.proj[2, 2], (cn.proj[2, 3] - 1) / cn.proj[2, 2])
+    fo, vd_f, vd_b = -co.view[2, :3], view_depth(co, float(zf)), view_depth(co, float(zb))
+
+    def grid_of(p):
+        hc = M @ np.append(p, 1.0)
+        return (hc[0] / hc[3] + 1) * 0.5 * w, (1 - hc[1] / hc[3]) * 0.5 * h
+
+    def crossed(o, d, s0, s1):
+        """(lists crossed, tie) for the segment s in [s0, s1] of the ray."""
+        (ax, ay), (bx, by) = grid_of(o + s0 * d), grid_of(o + s1 * d)
+        # an end on an interior grid line (ends on the frustum's sides, grid 0 or w, are no tie)
+        tie = any(abs(g - round(g)) < 1e-9 and 0 < round(g) < n
+                  for g, n in ((ax, w), (ay, h), (bx, w), (by, h)))
+        kx, ky = lines_between(ax, bx, w), lines_between(ay, by, h)
+        for k in kx:  # a corner: an x line met where y is also on a line
+            lam = (k - ax) / (bx - ax)
+            tie |= abs((ay + lam * (by - ay)) - round(ay + lam * (by - ay))) < 1e-9
+        return 1 + len(kx) + len(ky), tie
+
+    checked = crossings = 0
+    for q in range(W * H):
+        o, d = origins[q], dirs[q]
+        s0, s1 = clip_interval(o, d, planes, nN, fN)
+        if not s1 > s0 + 1e-12:
+            assert nl[q] == 0 and nsg[q] == 0
+            checked += 1
+            continue
+        want_l, tie = crossed(o, d, s0, s1)
+        # part of the ray between the slab's planes of constant V_O view depth
+        base, rate = fo @ (o - co.eye), fo @ d
+        ta, tb = sorted([(vd_f - base) / rate, (vd_b - base) / rate])
+        ca, cb = max(s0, ta), min(s1, tb)
+        if cb > ca + 1e-12:
+            # pieces inside the slab: lists crossed by [ca, cb] that are not empty
+            (ax, ay), (bx, by) = grid_of(o + ca * d), grid_of(o + cb * d)
+            want_s, tie2 = crossed(o, d, ca, cb)
+            tie |= tie2
+            # walk the crossed lists in order to drop the empty ones
+            ts = [0.0, 1.0] + [(k - ax) / (bx - ax) for k in lines_between(ax, bx, w)] + \
+                 [(k - ay) / (by - ay) for k in lines_between(ay, by, h)]
+            ts = sorted(ts)
+            want_s = 0
+            for t0, t1 in zip(ts, ts[1:]):
+                if t1 - t0 < 1e-12:
+                    continue
+                # the grid point at the middle of the NDC sub-segment (NDC is affine in the
+                # sub-segment's own parameter, which is what the crossings above measure)
+                gx, gy = ax + 0.5 * (t0 + t1) * (bx - ax), ay + 0.5 * (t0 + t1) * (by - ay)
+                ix, iy = min(int(gx), w - 1), min(int(gy), h - 1)
+                want_s += 0 if empty[iy, ix] else 1
+        else:
+            want_s = 0
+        if tie:
+            continue
+        assert nl[q] == want_l, (q, nl[q], want_l)
+        assert nsg[q] == want_s, (q, nsg[q], want_s)
+        checked += 1
+        crossings += want_l - 1
+    assert checked > 0.97 * W * H and crossings > 200
