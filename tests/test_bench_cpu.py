@@ -17,7 +17,12 @@ def test_reference_arm_prints_one_json_line():
     d = json.loads(lines[0])
     assert d["impl"] == "reference" and d["unit"] == "frames/s" and d["higher_is_better"] is True
     assert d["n_gpus"] == 1 and d["steps"] == 2 and d["warmup"] == 1 and d["data"] == "synthetic"
-    assert d["value"] > 0 and abs(d["ms_per_step"] - 1e3 / d["value"]) < 1e-6 * d["ms_per_step"]
+    # ms_per_step is the measured time of a sampled step; value extrapolates its rays/s to
+    # whole frames (on the tiny workload a step's sample has a whole frame's ray count)
+    assert d["value"] > 0 and abs(d["extrapolated_s_per_full_step"] * d["value"] - 1.0) < 1e-9
+    assert abs(d["ms_per_step"] - 1e3 * d["measured_s_per_step"]) < 1e-6 * d["ms_per_step"]
+    assert abs(d["ms_per_step"] - 1e3 / d["value"]) < 1e-6 * d["ms_per_step"]
+    assert d["rays_per_s"] > 0
     assert d["config"]["workload"].startswith("blobs 64^3")
     cb = d["cpu_baseline"]
     assert cb["kind"] == "oracle" and cb["cores"] >= 1 and cb["value"] == d["value"] and cb["sample"]

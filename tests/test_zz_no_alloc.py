@@ -5,12 +5,16 @@ an allocator, programs that allocate only at start-up).  Its low-resolution
 preview image lives in a fixed static buffer of the library.
 
 Collected last on purpose: run alone in a fresh process or after every other
-test, two calls in a row must each match vdi_render of the same view."""
+test, two calls in a row must each equal vdi_render of the same view bit for
+bit, and a call must not raise the high-water mark of the device's
+stream-ordered memory pool (where vdi_render takes its preview scratch)."""
+import ctypes
+
 import numpy as np
 import pytest
 
 import vdi_synth as S
-from helpers import check_tolerance, random_case
+from helpers import random_case
 
 pytestmark = pytest.mark.gpu
 torch = pytest.importorskip("torch")
@@ -44,7 +48,51 @@ def test_two_calls_in_a_row_match_vdi_render(setup):
         got = render(V, V.vdi_render_preview_static, vdi, cam, W, H, d_i, d_r)
         ref = render(V, V.vdi_render, vdi, cam, W, H, d_i, d_r)
         assert ref[..., 3].max() > 0.2
-        check_tolerance(got, ref, 0, what=f"static preview {W}x{H} d_i={d_i} d_r={d_r}")
+        assert np.array_equal(got, ref), f"static preview {W}x{H} d_i={d_i} d_r={d_r}"
+
+
+class _Pool:
+    """High-water mark of the device's current stream-ordered memory pool, read
+    through the CUDA runtime the library itself links (libcudart.so.13)."""
+
+    USED_MEM_CURRENT, USED_MEM_HIGH = 7, 8  # cudaMemPoolAttr
+
+    def __init__(self, device=0):
+        self.rt = ctypes.CDLL("libcudart.so.13")
+        self.pool = ctypes.c_void_p()
+        assert self.rt.cudaDeviceGetMemPool(ctypes.byref(self.pool), device) == 0
+
+    def attr(self, a):
+        v = ctypes.c_uint64()
+        assert self.rt.cudaMemPoolGetAttribute(self.pool, a, ctypes.byref(v)) == 0
+        return v.value
+
+    def reset_high(self):
+        zero = ctypes.c_uint64(0)  # the high-water mark can only be reset (to the current use)
+        assert self.rt.cudaMemPoolSetAttribute(self.pool, self.USED_MEM_HIGH, ctypes.byref(zero)) == 0
+        return self.attr(self.USED_MEM_HIGH)
+
+
+def test_no_device_allocation(setup):
+    """The static-buffer preview leaves the pool's high-water mark where it was;
+    vdi_render of the same preview raises it by its scratch image."""
+    V, case, vdi = setup
+    W, H, d_i, d_r = 1280, 720, 2, 1
+    cam = S.orbit_camera(case.bmin, case.bmax, W / H, az_deg=15.0, el_deg=20.0)
+    out = torch.zeros((H, W, 4), dtype=torch.float32, device="cuda")
+    args = (vdi, V.camera(cam.view, cam.proj), W, H, d_i, d_r, out, V.VDI_F32)
+    V.vdi_render_preview_static(*args)  # first call on the device: the buffer's address is looked up
+    torch.cuda.synchronize()
+    pool = _Pool(0)
+    base = pool.reset_high()
+    V.vdi_render_preview_static(*args)
+    torch.cuda.synchronize()
+    assert pool.attr(pool.USED_MEM_HIGH) == base
+    base = pool.reset_high()
+    V.vdi_render(*args)
+    torch.cuda.synchronize()
+    scratch = (-(-W // d_i)) * (-(-H // d_i)) * 16
+    assert pool.attr(pool.USED_MEM_HIGH) >= base + scratch
 
 
 def test_oversized_preview_is_rejected(setup):
