@@ -112,6 +112,11 @@ typedef struct {
     int blocks;          /* 1: skip 4 x 4 blocks of lists whose merged depth range the ray misses.
                             Off by default (measured slower on the benchmark workloads); the image
                             is bit-identical either way. */
+    int record_stats;    /* 1: count this frame's rays, lists and supersegment pieces into the
+                            VDI's totals, read back by vdi_stats (exact renders only, d_r = 1; the
+                            rays walk every list as with ray_lists; temporary per-ray counters
+                            come from the stream-ordered allocator when ray_lists / ray_segs are
+                            NULL) */
 } vdi_render_opts;
 
 /* ---- context ---------------------------------------------------------- */
@@ -165,6 +170,30 @@ vdi_status vdi_download(vdi_t *vdi, float *rgba, float *depth, int32_t *counts, 
 
 /* Layout of an existing VDI. */
 vdi_status vdi_get_layout(const vdi_t *vdi, vdi_layout *out);
+
+/* What a resident VDI holds and what its last counted frame did.  Sizes:
+ * Section 5 stores a VDI as an RGBA32F colour texture plus an R32F texture
+ * holding front and back depth (24 B per slot: 950 MiB at 1920 x 1080,
+ * N_S = 20, Section 6.3), and a count grid of 2.5 MiB at 1920 x 1080
+ * (Section 4.3); `layout` gives this library's bytes per array and the
+ * paper-layout size.  Frame totals: the last vdi_render_ex call with
+ * record_stats = 1 on this VDI, summed over its rays (Section 4.1: the lists
+ * a ray passes through; Section 4.2 / Eq. 2: the supersegment pieces it
+ * composites; with early termination unless no_ert).  Reading the totals
+ * synchronises `stream` (the stream that render was ordered on).  Before any
+ * counted frame, frame_recorded is 0 and the totals are 0. */
+typedef struct {
+    vdi_layout layout;      /* device bytes by array, grid dims, slots stored per list */
+    int w, h, n_s;          /* lists and supersegments per list */
+    int colour_fmt;         /* VDI_F32 or VDI_F16 */
+    int grid_tile;          /* lists per grid cell side */
+    int frame_recorded;     /* 1 when the totals below describe a counted frame */
+    int frame_w, frame_h;   /* rays of that frame (after d_i) */
+    uint64_t rays_hit;      /* rays that passed through at least one list with positive length */
+    uint64_t lists;         /* lists passed through with positive length, summed over the rays */
+    uint64_t pieces;        /* supersegment pieces of positive length composited, summed over the rays */
+} vdi_stats_t;
+vdi_status vdi_stats(vdi_t *vdi, vdi_stats_t *out, void *stream);
 
 /* Free the VDI's device memory.  Stream-ordered on the stream it was created
  * on; the caller must not destroy a VDI that other streams still render. */
@@ -454,13 +483,20 @@ vdi_status vdi_search_first(vdi_t *vdi, int list, int search, const float *d_ent
 /* Mark, in a caller-provided zeroed DEVICE bitmap, every 4-byte word of the
  * VDI's depth and colour arrays that an exact render (d_i = d_r = 1,
  * Algorithm 2) of `view` at W x H reads under the method's access rule
- * (Section 4.2: the two depths of the seed probe, one depth per binary-search
- * probe, front/back depth of each supersegment walked, the colour record of
- * each supersegment piece composited).  Bit w of word w / 32 stands for byte
- * offset 4 w of the depth array followed by the colour array; `words` is the
- * bitmap length in uint32 and must be at least
- * ceil((depth_bytes + colour_bytes) / 128).  The popcount times 4 is the
- * number of unique VDI bytes one frame needs (the roofline numerator). */
+ * (Section 4.2: per list passed through, its depth range (front of the
+ * first, back of the last supersegment); the two depths of Algorithm 2's seed
+ * probe, one depth per binary-search probe, front/back depth of each
+ * supersegment walked, the colour record of each supersegment piece
+ * composited).  Bit (w mod 32) of word w / 32 stands for the 4-byte word w of
+ * the VDI's device arrays laid end to end (vdi_layout_bytes): the depth array
+ * ([n_s_stored / 2][h*w] records of (f_2k, b_2k, f_2k+1, b_2k+1)), the colour
+ * array (FP32: [n_s_stored][h*w] records of 4 words; FP16: [n_s_stored / 2][h*w]
+ * records holding two slots of 2 words), the count grid
+ * (grid_nz * grid_h * grid_w words, padded to a multiple of 4) and the list
+ * ranges ([h*w] pairs (front, back)).  `words` is the bitmap length in uint32
+ * and must be at least ceil((depth_bytes + colour_bytes + 4 * grid words
+ * + list_bytes) / 128).  The popcount times 4 is the number of unique VDI
+ * bytes one frame needs (the roofline numerator). */
 vdi_status vdi_touch_bitmap(vdi_t *vdi, const vdi_camera *view, int W, int H, uint32_t *bitmap, size_t words,
                             void *stream);
 

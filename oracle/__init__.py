@@ -66,6 +66,9 @@ def lib():
         L.orc_grid_edges.argtypes = [P, C.c_int, P]
         L.orc_grid_counts.argtypes = [P, C.c_int, C.c_int, P]
         L.orc_render_preview.argtypes = [P, P, C.c_int, C.c_int, C.c_int, P, P, C.c_int, P, P, C.c_int]
+        L.orc_render_preview_alt.argtypes = [P, P, C.c_int, C.c_int, C.c_int, P, P, C.c_int, P, P, P, C.c_int]
+        L.orc_render_exact_ndc.argtypes = [P, P, P, C.c_int, P, P, P, P, C.c_int]
+        L.orc_touch_exact.argtypes = [P, P, P, C.c_int, C.c_int, P, P, P, P]
         L.orc_upsample.argtypes = [P, C.c_int, C.c_int, P, C.c_int, C.c_int]
         L.orc_first_index.argtypes = [P, P, C.c_int, C.c_float, C.c_float, C.c_int]
         L.orc_first_index.restype = C.c_int
@@ -178,6 +181,58 @@ def render_preview(scene, view, proj, W, H, d_r, T=8, nz=20, grid=None, pix=None
                                   _ptr(grid), _ptr(p), n, _ptr(out), _ptr(fl), nthreads)
     assert rc == 0
     return out, fl
+
+
+def render_preview_alt(scene, view, proj, W, H, d_r, T, nz, grid, pix, alt, nthreads=None):
+    """D_R preview of the pixels ``pix`` with near-tie decisions flipped: pixel q
+    flips the decisions whose bits are set in ``alt[q]`` (alt = 0: the plain
+    rule).  Returns (rgba[n,4] f64, number of tie decisions each ray met)."""
+    nthreads = nthreads or os.cpu_count()
+    grid = np.ascontiguousarray(grid, np.uint32)
+    p = np.ascontiguousarray(pix, np.int32)
+    a = np.ascontiguousarray(np.broadcast_to(np.asarray(alt, np.uint32), p.shape), np.uint32)
+    out = np.zeros((len(p), 4), np.float64)
+    nt = np.zeros(len(p), np.int32)
+    v = _view(view, proj, W, H)
+    rc = lib().orc_render_preview_alt(C.byref(scene.s), C.byref(v), int(d_r), int(T), int(nz), _ptr(grid), _ptr(p),
+                                      len(p), _ptr(a), _ptr(out), _ptr(nt), nthreads)
+    assert rc == 0
+    return out, nt
+
+
+def render_exact_ndc(scene, view, proj, xy, nthreads=None):
+    """Exact render of rays through V_N NDC points xy[n, 2].  Returns
+    (rgba[n,4] f64, n_lists, n_segs, flags) as render_exact."""
+    nthreads = nthreads or os.cpu_count()
+    xy = np.ascontiguousarray(xy, np.float64).reshape(-1, 2)
+    n = len(xy)
+    out = np.zeros((n, 4), np.float64)
+    nl = np.zeros(n, np.int32)
+    ns = np.zeros(n, np.int32)
+    fl = np.zeros(n, np.uint8)
+    v = _view(view, proj, 1, 1)
+    rc = lib().orc_render_exact_ndc(C.byref(scene.s), C.byref(v), _ptr(xy), n, _ptr(out), _ptr(nl), _ptr(ns),
+                                    _ptr(fl), nthreads)
+    assert rc == 0
+    return out, nl, ns, fl
+
+
+def touch_exact(scene, view, proj, W, H, pix=None):
+    """Replay of the exact render's access rule (Section 4.2, Algorithm 2) over
+    the rays of ``pix`` (all pixels if None).  Returns (depth[h*w, nsp, 2],
+    colour[h*w, nsp], range[h*w]) boolean masks of what the rays read, and the
+    per-ray flags of reads that turn on a near-tie decision."""
+    nsp = scene.ns + (scene.ns & 1)
+    nl = scene.w * scene.h
+    p, n = _pix(pix, W, H)
+    dm = np.zeros((nl, nsp, 2), np.uint8)
+    cm = np.zeros((nl, nsp), np.uint8)
+    rm = np.zeros(nl, np.uint8)
+    fl = np.zeros(n, np.uint8)
+    v = _view(view, proj, W, H)
+    rc = lib().orc_touch_exact(C.byref(scene.s), C.byref(v), _ptr(p), n, nsp, _ptr(dm), _ptr(cm), _ptr(rm), _ptr(fl))
+    assert rc == 0
+    return dm.astype(bool), cm.astype(bool), rm.astype(bool), fl
 
 
 def upsample(lo, w0, h0, W, H):

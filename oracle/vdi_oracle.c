@@ -388,6 +388,196 @@ ORC_EXPORT int orc_render_exact(const orc_vdi *V, const orc_view *N, const int32
     return 0;
 }
 
+/* The exact render of rays through explicit V_N NDC points (x, y) = xy[2q],
+ * xy[2q+1]: a pixel centre moved by a small offset is a ray the rounding of
+ * a finite-precision renderer can stand for, so it gives the other valid
+ * values of a ray that runs along a list boundary. */
+ORC_EXPORT int orc_render_exact_ndc(const orc_vdi *V, const orc_view *N, const double *xy, int n, double *out,
+                                    int32_t *n_lists, int32_t *n_segs, uint8_t *flags, int nthreads) {
+    oview ov;
+    if (!make_oview(V, N, &ov) || !xy) return 1;
+    int bufn = V->w + V->h + 8, zbn = 2 * V->ns + 4;
+#pragma omp parallel num_threads(nthreads > 0 ? nthreads : 1)
+    {
+        double *tb = malloc(sizeof(double) * bufn);
+        double *zb = malloc(sizeof(double) * zbn);
+#pragma omp for schedule(dynamic, 64)
+        for (int q = 0; q < n; q++)
+            exact_pixel(V, &ov, xy[2 * q], xy[2 * q + 1], tb, zb, out + (size_t)q * 4, n_lists ? n_lists + q : NULL,
+                        n_segs ? n_segs + q : NULL, flags ? flags + q : NULL);
+        free(tb);
+        free(zb);
+    }
+    return 0;
+}
+
+/* ------------------------------------------------------------------ */
+/* Bytes-touched replay (the roofline numerator's access rule)          */
+/*                                                                      */
+/* Which VDI values an exact render reads, by the rule the method's    */
+/* traversal defines (Section 4.2, Algorithm 2): per list the ray       */
+/* passes through with positive length, its depth range (front of the   */
+/* first and back of the last supersegment: a ray that meets neither    */
+/* reads nothing else there); Algorithm 2's seed probe reads two        */
+/* depths (the seed rounded to the odd slot q, so b_{q-1}, b_q for      */
+/* depth increasing along the ray; the even slot q and f_q, f_{q+1}     */
+/* when it decreases), each binary-search probe one depth (b_mid, or    */
+/* f_mid); each supersegment walked its front and back depth; each      */
+/* piece of positive length its colour.  The seed is carried from list  */
+/* to list (the last supersegment met, else the search's answer); the   */
+/* first list has seed 0 when depth increases along the ray and none    */
+/* (plain binary search) when it decreases.  Compositing stops once     */
+/* transmittance <= 2^-12.  Lists hold nsp slots (N_S rounded up to     */
+/* even); slots past a list's count read as +inf.                       */
+/*                                                                      */
+/* Output: per list li, slot j: depth_mask[(li*nsp + j)*2 + (0 front,   */
+/* 1 back)], colour_mask[li*nsp + j], range_mask[li]; the union over    */
+/* the rays of pix.  flags[q] marks a ray whose reads turn on a         */
+/* decision within rounding distance of a tie (the exact render's       */
+/* flags, or a transmittance within 1e-3 of the termination bound).    */
+/* ------------------------------------------------------------------ */
+
+static double slot_f(const orc_vdi *V, int li, int j) { return j < list_count(V, li) ? seg_f(V, li, j) : INFINITY; }
+static double slot_b(const orc_vdi *V, int li, int j) { return j < list_count(V, li) ? seg_b(V, li, j) : INFINITY; }
+
+ORC_EXPORT int orc_touch_exact(const orc_vdi *V, const orc_view *N, const int32_t *pix, int npix, int nsp,
+                               uint8_t *depth_mask, uint8_t *colour_mask, uint8_t *range_mask, uint8_t *flags) {
+    oview ov;
+    if (!make_oview(V, N, &ov) || nsp < V->ns || (nsp & 1)) return 1;
+    if (!pix) npix = N->W * N->H;
+    const double T_end = 1.0 / 4096.0;
+    double *tb = malloc(sizeof(double) * (V->w + V->h + 8));
+    for (int q = 0; q < npix; q++) {
+        int px, py;
+        pixel_of(pix, q, N->W, &px, &py);
+        double x, y;
+        pixel_ndc(px, py, N->W, N->H, &x, &y);
+        /* the exact render's own flags for this ray */
+        double zb_unused[2 * 64 + 4], acc_unused[4];
+        uint8_t fl = 0;
+        if (V->ns <= 64) exact_pixel(V, &ov, x, y, tb, zb_unused, acc_unused, NULL, NULL, &fl);
+        oray r;
+        if (setup_ray(V, &ov, x, y, &r)) {
+            double p0[3], p1[3], g0x, g0y, g1x, g1y;
+            ndc_at(&r, r.t0, p0);
+            ndc_at(&r, r.t1, p1);
+            grid_xy(V, p0, &g0x, &g0y);
+            grid_xy(V, p1, &g1x, &g1y);
+            const int inc = p1[2] - p0[2] >= 0.0;
+            if (fabs(p1[2] - p0[2]) < 1e-6) fl = 1; /* depth direction itself near a tie */
+            /* the ray's pieces in list order, as in the exact render */
+            int nb = 0;
+            tb[nb++] = r.t0;
+            tb[nb++] = r.t1;
+            double lo = fmin(g0x, g1x), hi = fmax(g0x, g1x);
+            for (int k = (int)floor(lo) + 1; k < hi && k < V->w; k++) {
+                double t;
+                if (k > 0 && (double)k > lo && cross_t(&r, 0, -1.0 + 2.0 * k / V->w, &t) && t > r.t0 && t < r.t1)
+                    tb[nb++] = t;
+            }
+            lo = fmin(g0y, g1y);
+            hi = fmax(g0y, g1y);
+            for (int k = (int)floor(lo) + 1; k < hi && k < V->h; k++) {
+                double t;
+                if (k > 0 && (double)k > lo && cross_t(&r, 1, 1.0 - 2.0 * k / V->h, &t) && t > r.t0 && t < r.t1)
+                    tb[nb++] = t;
+            }
+            qsort(tb, nb, sizeof(double), cmp_double);
+            double acc[4] = {0, 0, 0, 0};
+            int p = inc ? 0 : -1, done = 0;
+            for (int s = 0; s + 1 < nb && !done; s++) {
+                double ta = tb[s], tbb = tb[s + 1];
+                if (!(tbb > ta)) continue;
+                double pm[3], pa[3], pb[3], gx, gy;
+                ndc_at(&r, 0.5 * (ta + tbb), pm);
+                grid_xy(V, pm, &gx, &gy);
+                int li = clampi((int)floor(gy), 0, V->h - 1) * V->w + clampi((int)floor(gx), 0, V->w - 1);
+                ndc_at(&r, ta, pa);
+                ndc_at(&r, tbb, pb);
+                double d_in = pa[2], d_out = pb[2];
+                int n = list_count(V, li);
+                range_mask[li] = 1;
+                double rf = n > 0 ? seg_f(V, li, 0) : INFINITY, rb = n > 0 ? seg_b(V, li, n - 1) : -INFINITY;
+                if (fmax(d_in, d_out) < rf || fmin(d_in, d_out) > rb) continue; /* nothing met in this list */
+#define MARK_D(j, which) (depth_mask[((size_t)li * nsp + (j)) * 2 + (which)] = 1)
+                int first;
+                if (inc) {
+                    /* first = min{ j : b_j >= d_in } over [0, nsp), nsp if none */
+                    int a = 0, b = nsp;
+                    if (p >= 0) {
+                        int qq = p | 1;
+                        if (qq >= nsp) qq = nsp - 1;
+                        MARK_D(qq - 1, 1);
+                        MARK_D(qq, 1);
+                        int ge = (slot_b(V, li, qq) >= d_in) + (slot_b(V, li, qq - 1) >= d_in);
+                        if (ge == 1) a = b = qq;
+                        else if (ge == 2) { a = 0; b = qq - 1; }
+                        else { a = qq + 1; b = nsp; }
+                    }
+                    while (a < b) {
+                        int mid = (a + b) / 2;
+                        MARK_D(mid, 1);
+                        if (slot_b(V, li, mid) >= d_in) b = mid; else a = mid + 1;
+                    }
+                    first = a;
+                } else {
+                    /* first = max{ j : f_j <= d_in } over [0, nsp), -1 if none */
+                    int a = -1, b = nsp - 1;
+                    if (p >= 0) {
+                        int qq = p & ~1;
+                        if (qq >= nsp) qq = nsp - 2;
+                        MARK_D(qq, 0);
+                        MARK_D(qq + 1, 0);
+                        int le = (slot_f(V, li, qq) <= d_in) + (slot_f(V, li, qq + 1) <= d_in);
+                        if (le == 1) a = b = qq;
+                        else if (le == 2) { a = qq + 1; b = nsp - 1; }
+                        else { a = -1; b = qq - 1; }
+                    }
+                    while (a < b) {
+                        int mid = (a + b + 1) / 2;
+                        MARK_D(mid, 0);
+                        if (slot_f(V, li, mid) <= d_in) a = mid; else b = mid - 1;
+                    }
+                    first = a;
+                }
+                /* walk the supersegments in the ray's depth order */
+                int last = -1;
+                for (int j = first; j >= 0 && j < nsp; j += inc ? 1 : -1) {
+                    double f = slot_f(V, li, j), b = slot_b(V, li, j);
+                    MARK_D(j, 0);
+                    MARK_D(j, 1);
+                    if (inc ? (f > d_out) : (b < d_out)) break;
+                    last = j;
+                    /* overlap of [f, b] with the piece's depth range, as ray parameters */
+                    double za = inc ? fmax(f, d_in) : fmin(b, d_in), zbb = inc ? fmin(b, d_out) : fmax(f, d_out);
+                    if (inc ? (zbb > za) : (zbb < za)) {
+                        double tza, tzb;
+                        if (!cross_t(&r, 2, za, &tza)) tza = ta;
+                        if (!cross_t(&r, 2, zbb, &tzb)) tzb = tbb;
+                        tza = fmin(fmax(tza, ta), tbb);
+                        tzb = fmin(fmax(tzb, ta), tbb);
+                        colour_mask[(size_t)li * nsp + j] = 1;
+                        composite(acc, seg_rgba(V, li, j), r.len * fabs(tzb - tza), V->u);
+                        double Tr = 1.0 - acc[3];
+                        if (fabs(Tr - T_end) < 1e-3 * T_end) fl = 1;
+                        if (Tr <= T_end) {
+                            done = 1;
+                            break;
+                        }
+                    }
+                    if (inc ? (b > d_out) : (f < d_out)) break;
+                }
+#undef MARK_D
+                p = (last >= 0) ? last : first;
+                if (p < 0) p = 0;
+            }
+        }
+        if (flags) flags[q] = fl;
+    }
+    free(tb);
+    return 0;
+}
+
 /* ------------------------------------------------------------------ */
 /* O-sampled: brute-force midpoint sampling at world step ~h           */
 /* ------------------------------------------------------------------ */
@@ -543,17 +733,181 @@ ORC_EXPORT int orc_grid_counts(const orc_vdi *V, int T, int nz, uint32_t *grid) 
 #define EPS_SAMPLE_Z 5e-6
 #define EPS_COUNT 1e-4
 
+typedef struct {
+    int T, nz, gw, gh, d_r;
+    const uint32_t *grid;
+    const float *edges;
+    double dz_cell; /* view-depth extent of one slab */
+} preview_grid;
+
+/* Decision number k of a ray (counted in the order the ray meets them) takes
+ * its other side when bit k of `alt` is set. */
+static int take_other(unsigned alt, int k) { return k < 32 && ((alt >> k) & 1u); }
+
+/* One D_R preview ray through V_N NDC (x, y).  Decisions that sit within
+ * rounding distance of a tie are counted in *n_tie: a sample count
+ * (c/F)(l_c/dz)/D_R within EPS_COUNT of an integer (other side: the
+ * neighbouring count), a sample within EPS_GRID list widths of an interior
+ * list boundary (other side: the list across it), a sample within
+ * EPS_SAMPLE_Z of a supersegment face of its list (other side: the
+ * containment test just across that face).  With alt = 0 every decision is
+ * the plain rule.  *flag also marks cell boundaries crossed close together or
+ * close to a ray end (pieces of vanishing length; they move the result
+ * continuously). */
+static void preview_pixel(const orc_vdi *V, const oview *ov, const preview_grid *G, double x, double y,
+                          unsigned alt, double *tb, double acc[4], int *n_tie, uint8_t *flag) {
+    const int T = G->T, nz = G->nz;
+    const float *edges = G->edges;
+    int fl = 0, tie = 0;
+    acc[0] = acc[1] = acc[2] = acc[3] = 0.0;
+    oray r;
+    if (setup_ray(V, ov, x, y, &r)) {
+        int nb = 0;
+        tb[nb++] = r.t0;
+        tb[nb++] = r.t1;
+        double p0[3], p1[3];
+        ndc_at(&r, r.t0, p0);
+        ndc_at(&r, r.t1, p1);
+        /* cell boundaries in x (every T lists), y (every T rows), z (slab edges) */
+        for (int k = 1; k * T < V->w; k++) {
+            double X = -1.0 + 2.0 * (k * T) / V->w, t;
+            if ((p0[0] - X) * (p1[0] - X) < 0.0 && cross_t(&r, 0, X, &t) && t > r.t0 && t < r.t1) tb[nb++] = t;
+        }
+        for (int k = 1; k * T < V->h; k++) {
+            double Y = 1.0 - 2.0 * (k * T) / V->h, t;
+            if ((p0[1] - Y) * (p1[1] - Y) < 0.0 && cross_t(&r, 1, Y, &t) && t > r.t0 && t < r.t1) tb[nb++] = t;
+        }
+        for (int k = 1; k < nz; k++) {
+            double Z = edges[k], t;
+            if ((p0[2] - Z) * (p1[2] - Z) < 0.0 && cross_t(&r, 2, Z, &t) && t > r.t0 && t < r.t1) tb[nb++] = t;
+        }
+        qsort(tb, nb, sizeof(double), cmp_double);
+        /* flag: a cell boundary crossing close to another cell boundary */
+        for (int s = 0; s < nb; s++) {
+            double p[3], gx, gy;
+            ndc_at(&r, tb[s], p);
+            grid_xy(V, p, &gx, &gy);
+            double cx = gx / T, cy = gy / T;
+            int nearx = near_interior_line(gx, V->w, EPS_GRID) && frac_dist(cx) * T < EPS_GRID;
+            int neary = near_interior_line(gy, V->h, EPS_GRID) && frac_dist(cy) * T < EPS_GRID;
+            int nearz = 0;
+            for (int k = 1; k < nz; k++)
+                if (fabs(p[2] - edges[k]) < EPS_SAMPLE_Z) nearz = 1;
+            if (nearx + neary + nearz >= 2) fl = 1;
+            if ((s == 0 || s == nb - 1) && (nearx || neary || nearz)) fl = 1;
+        }
+        for (int s = 0; s + 1 < nb; s++) {
+            double ta = tb[s], tbb = tb[s + 1];
+            if (!(tbb > ta)) continue;
+            double pm[3], gx, gy;
+            ndc_at(&r, 0.5 * (ta + tbb), pm);
+            grid_xy(V, pm, &gx, &gy);
+            int ix = clampi((int)floor(gx), 0, V->w - 1);
+            int iy = clampi((int)floor(gy), 0, V->h - 1);
+            int cz = 0;
+            while (cz + 1 < nz && pm[2] >= edges[cz + 1]) cz++;
+            int cx = ix / T, cy = iy / T;
+            uint32_t c = G->grid[((size_t)cz * G->gh + cy) * G->gw + cx];
+            if (c == 0) continue;
+            int fx = ((cx + 1) * T < V->w ? T : V->w - cx * T);
+            int fy = ((cy + 1) * T < V->h ? T : V->h - cy * T);
+            double lc = r.len * (tbb - ta);
+            double want = ((double)c / (double)(fx * fy)) * (lc / G->dz_cell) / (double)G->d_r;
+            long n = (long)ceil(want);
+            if (fabs(want - floor(want + 0.5)) < EPS_COUNT * fmax(1.0, want)) {
+                fl = 1;
+                if (take_other(alt, tie++)) {
+                    long k = (long)floor(want + 0.5);
+                    n = (n == k) ? k + 1 : k;
+                }
+            }
+            if (n < 1) n = 1;
+            double spacing = lc / (double)n;
+            for (long k = 0; k < n; k++) {
+                double t = ta + (tbb - ta) * ((double)k + 0.5) / (double)n;
+                double p[3], sx, sy;
+                ndc_at(&r, t, p);
+                grid_xy(V, p, &sx, &sy);
+                int jx = clampi((int)floor(sx), 0, V->w - 1);
+                int jy = clampi((int)floor(sy), 0, V->h - 1);
+                if (near_interior_line(sx, V->w, EPS_GRID)) {
+                    fl = 1;
+                    if (take_other(alt, tie++)) {
+                        int L = (int)floor(sx + 0.5);
+                        jx = (jx >= L) ? L - 1 : L;
+                    }
+                }
+                if (near_interior_line(sy, V->h, EPS_GRID)) {
+                    fl = 1;
+                    if (take_other(alt, tie++)) {
+                        int L = (int)floor(sy + 0.5);
+                        jy = (jy >= L) ? L - 1 : L;
+                    }
+                }
+                int li = jy * V->w + jx, nn = list_count(V, li);
+                /* the face of this list nearest to the sample, if within EPS_SAMPLE_Z */
+                double z = p[2], best = EPS_SAMPLE_Z, face = 0.0;
+                int face_kind = -1; /* 0 front, 1 back */
+                for (int j = 0; j < nn; j++) {
+                    double f = seg_f(V, li, j), b = seg_b(V, li, j);
+                    if (fabs(z - f) < best) {
+                        best = fabs(z - f);
+                        face = f;
+                        face_kind = 0;
+                    }
+                    if (fabs(z - b) < best) {
+                        best = fabs(z - b);
+                        face = b;
+                        face_kind = 1;
+                    }
+                }
+                if (face_kind >= 0) {
+                    fl = 1;
+                    if (take_other(alt, tie++)) {
+                        /* inside a front face means z >= f, inside a back face z <= b */
+                        const double step = 1e-12;
+                        if (face_kind == 0)
+                            z = (z >= face) ? face - step : face + step;
+                        else
+                            z = (z <= face) ? face + step : face - step;
+                    }
+                }
+                int hit = -1;
+                for (int j = 0; j < nn && hit < 0; j++)
+                    if (seg_f(V, li, j) <= z && z <= seg_b(V, li, j)) hit = j;
+                if (hit >= 0) composite(acc, seg_rgba(V, li, hit), spacing, V->u);
+            }
+        }
+    }
+    if (n_tie) *n_tie = tie;
+    if (flag) *flag = (uint8_t)fl;
+}
+
+static int preview_setup(const orc_vdi *V, int d_r, int T, int nz, const uint32_t *grid, preview_grid *G) {
+    if (d_r < 1 || T < 1 || nz < 1 || !grid) return 0;
+    float *edges = malloc(sizeof(float) * (nz + 1));
+    orc_grid_edges(V, nz, edges);
+    G->T = T;
+    G->nz = nz;
+    G->d_r = d_r;
+    G->gw = (V->w + T - 1) / T;
+    G->gh = (V->h + T - 1) / T;
+    G->grid = grid;
+    G->edges = edges;
+    double dn = view_depth_of_ndc(V->proj_o, -1.0), df = view_depth_of_ndc(V->proj_o, 1.0);
+    G->dz_cell = (df - dn) / nz;
+    return 1;
+}
+
+/* The D_R preview of every pixel (or of the listed ones), with per-pixel
+ * flags for rays that meet a tie (see preview_pixel). */
 ORC_EXPORT int orc_render_preview(const orc_vdi *V, const orc_view *N, int d_r, int T, int nz,
                                   const uint32_t *grid, const int32_t *pix, int npix, double *out,
                                   uint8_t *flags, int nthreads) {
     oview ov;
-    if (!make_oview(V, N, &ov) || d_r < 1 || T < 1 || nz < 1) return 1;
+    preview_grid G;
+    if (!make_oview(V, N, &ov) || !preview_setup(V, d_r, T, nz, grid, &G)) return 1;
     if (!pix) npix = N->W * N->H;
-    float *edges = malloc(sizeof(float) * (nz + 1));
-    orc_grid_edges(V, nz, edges);
-    int gw = (V->w + T - 1) / T, gh = (V->h + T - 1) / T;
-    double dn = view_depth_of_ndc(V->proj_o, -1.0), df = view_depth_of_ndc(V->proj_o, 1.0);
-    double dz_cell = (df - dn) / nz;
     int bufn = (V->w / T + V->h / T + nz) + 16;
 #pragma omp parallel num_threads(nthreads > 0 ? nthreads : 1)
     {
@@ -562,95 +916,43 @@ ORC_EXPORT int orc_render_preview(const orc_vdi *V, const orc_view *N, int d_r, 
         for (int q = 0; q < npix; q++) {
             int px, py;
             pixel_of(pix, q, N->W, &px, &py);
-            double x, y, acc[4] = {0, 0, 0, 0};
-            int fl = 0;
+            double x, y;
             pixel_ndc(px, py, N->W, N->H, &x, &y);
-            oray r;
-            if (setup_ray(V, &ov, x, y, &r)) {
-                int nb = 0;
-                tb[nb++] = r.t0;
-                tb[nb++] = r.t1;
-                double p0[3], p1[3];
-                ndc_at(&r, r.t0, p0);
-                ndc_at(&r, r.t1, p1);
-                /* cell boundaries in x (every T lists), y (every T rows), z (slab edges) */
-                for (int k = 1; k * T < V->w; k++) {
-                    double X = -1.0 + 2.0 * (k * T) / V->w, t;
-                    if ((p0[0] - X) * (p1[0] - X) < 0.0 && cross_t(&r, 0, X, &t) && t > r.t0 && t < r.t1)
-                        tb[nb++] = t;
-                }
-                for (int k = 1; k * T < V->h; k++) {
-                    double Y = 1.0 - 2.0 * (k * T) / V->h, t;
-                    if ((p0[1] - Y) * (p1[1] - Y) < 0.0 && cross_t(&r, 1, Y, &t) && t > r.t0 && t < r.t1)
-                        tb[nb++] = t;
-                }
-                for (int k = 1; k < nz; k++) {
-                    double Z = edges[k], t;
-                    if ((p0[2] - Z) * (p1[2] - Z) < 0.0 && cross_t(&r, 2, Z, &t) && t > r.t0 && t < r.t1)
-                        tb[nb++] = t;
-                }
-                qsort(tb, nb, sizeof(double), cmp_double);
-                /* flag: a cell boundary crossing close to another cell boundary */
-                for (int s = 0; s < nb; s++) {
-                    double p[3], gx, gy;
-                    ndc_at(&r, tb[s], p);
-                    grid_xy(V, p, &gx, &gy);
-                    double cx = gx / T, cy = gy / T;
-                    int nearx = near_interior_line(gx, V->w, EPS_GRID) && frac_dist(cx) * T < EPS_GRID;
-                    int neary = near_interior_line(gy, V->h, EPS_GRID) && frac_dist(cy) * T < EPS_GRID;
-                    int nearz = 0;
-                    for (int k = 1; k < nz; k++)
-                        if (fabs(p[2] - edges[k]) < EPS_SAMPLE_Z) nearz = 1;
-                    if (nearx + neary + nearz >= 2) fl = 1;
-                    if ((s == 0 || s == nb - 1) && (nearx || neary || nearz)) fl = 1;
-                }
-                for (int s = 0; s + 1 < nb; s++) {
-                    double ta = tb[s], tbb = tb[s + 1];
-                    if (!(tbb > ta)) continue;
-                    double pm[3], gx, gy;
-                    ndc_at(&r, 0.5 * (ta + tbb), pm);
-                    grid_xy(V, pm, &gx, &gy);
-                    int ix = clampi((int)floor(gx), 0, V->w - 1);
-                    int iy = clampi((int)floor(gy), 0, V->h - 1);
-                    int cz = 0;
-                    while (cz + 1 < nz && pm[2] >= edges[cz + 1]) cz++;
-                    int cx = ix / T, cy = iy / T;
-                    uint32_t c = grid[((size_t)cz * gh + cy) * gw + cx];
-                    if (c == 0) continue;
-                    int fx = ((cx + 1) * T < V->w ? T : V->w - cx * T);
-                    int fy = ((cy + 1) * T < V->h ? T : V->h - cy * T);
-                    double lc = r.len * (tbb - ta);
-                    double want = ((double)c / (double)(fx * fy)) * (lc / dz_cell) / (double)d_r;
-                    if (fabs(want - floor(want + 0.5)) < EPS_COUNT * fmax(1.0, want)) fl = 1;
-                    long n = (long)ceil(want);
-                    if (n < 1) n = 1;
-                    double spacing = lc / (double)n;
-                    for (long k = 0; k < n; k++) {
-                        double t = ta + (tbb - ta) * ((double)k + 0.5) / (double)n;
-                        double p[3], sx, sy;
-                        ndc_at(&r, t, p);
-                        grid_xy(V, p, &sx, &sy);
-                        if (near_interior_line(sx, V->w, EPS_GRID) || near_interior_line(sy, V->h, EPS_GRID))
-                            fl = 1;
-                        int jx = clampi((int)floor(sx), 0, V->w - 1);
-                        int jy = clampi((int)floor(sy), 0, V->h - 1);
-                        int li = jy * V->w + jx, nn = list_count(V, li);
-                        int hit = -1;
-                        for (int j = 0; j < nn; j++) {
-                            double f = seg_f(V, li, j), b = seg_b(V, li, j);
-                            if (fabs(p[2] - f) < EPS_SAMPLE_Z || fabs(p[2] - b) < EPS_SAMPLE_Z) fl = 1;
-                            if (hit < 0 && f <= p[2] && p[2] <= b) hit = j;
-                        }
-                        if (hit >= 0) composite(acc, seg_rgba(V, li, hit), spacing, V->u);
-                    }
-                }
-            }
-            memcpy(out + (size_t)q * 4, acc, sizeof acc);
-            if (flags) flags[q] = (uint8_t)fl;
+            preview_pixel(V, &ov, &G, x, y, 0u, tb, out + (size_t)q * 4, NULL, flags ? flags + q : NULL);
         }
         free(tb);
     }
-    free(edges);
+    free((void *)G.edges);
+    return 0;
+}
+
+/* The D_R preview of the listed pixels with near-tie decisions flipped: pixel
+ * q flips the decisions whose bits are set in alt[q]; n_ties[q] returns how
+ * many tie decisions its ray met.  Every such result is a valid limit of the
+ * preview under rounding (the GPU decides each tie in FP32). */
+ORC_EXPORT int orc_render_preview_alt(const orc_vdi *V, const orc_view *N, int d_r, int T, int nz,
+                                      const uint32_t *grid, const int32_t *pix, int npix, const uint32_t *alt,
+                                      double *out, int32_t *n_ties, int nthreads) {
+    oview ov;
+    preview_grid G;
+    if (!make_oview(V, N, &ov) || !preview_setup(V, d_r, T, nz, grid, &G) || !pix || !alt) return 1;
+    int bufn = (V->w / T + V->h / T + nz) + 16;
+#pragma omp parallel num_threads(nthreads > 0 ? nthreads : 1)
+    {
+        double *tb = malloc(sizeof(double) * bufn);
+#pragma omp for schedule(dynamic, 16)
+        for (int q = 0; q < npix; q++) {
+            int px, py;
+            pixel_of(pix, q, N->W, &px, &py);
+            double x, y;
+            pixel_ndc(px, py, N->W, N->H, &x, &y);
+            int nt = 0;
+            preview_pixel(V, &ov, &G, x, y, alt[q], tb, out + (size_t)q * 4, &nt, NULL);
+            if (n_ties) n_ties[q] = nt;
+        }
+        free(tb);
+    }
+    free((void *)G.edges);
     return 0;
 }
 

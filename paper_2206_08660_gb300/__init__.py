@@ -20,7 +20,7 @@ from . import build as _build
 __all__ = [
     "VDI_F32", "VDI_F16", "VDI_MEM_HOST", "VDI_MEM_DEVICE", "VDI_SEARCH_ALG2", "VDI_SEARCH_BINARY",
     "VDI_SEARCH_LINEAR", "VdiError", "VdiCamera", "VdiDesc", "VdiLayout", "VdiRenderOpts", "load",
-    "vdi_ctx_create", "vdi_ctx_destroy", "vdi_layout_bytes", "vdi_create", "vdi_download", "vdi_get_layout",
+    "vdi_ctx_create", "vdi_ctx_destroy", "vdi_layout_bytes", "vdi_create", "vdi_download", "vdi_get_layout", "vdi_stats",
     "vdi_destroy", "vdi_render", "vdi_render_ex", "vdi_render_preview_static", "VDI_STATIC_PREVIEW_PIXELS", "vdi_search_first", "vdi_generate", "vdi_touch_bitmap", "vdi_render_batch", "vdi_autotune_batch", "request",
     "vdi_server_create", "vdi_server_set_vdi", "vdi_server_submit", "vdi_server_wait", "vdi_server_poll",
     "vdi_server_release", "vdi_server_read", "vdi_server_stats", "vdi_server_destroy", "VdiViewRequest", "VdiTicketInfo",
@@ -56,6 +56,12 @@ class VdiLayout(C.Structure):
     _fields_ = [("depth_bytes", C.c_size_t), ("colour_bytes", C.c_size_t), ("grid_bytes", C.c_size_t),
                 ("list_bytes", C.c_size_t), ("total_bytes", C.c_size_t), ("paper_bytes", C.c_size_t), ("grid_w", C.c_int),
                 ("grid_h", C.c_int), ("grid_nz", C.c_int), ("n_s_stored", C.c_int)]
+
+
+class VdiStats(C.Structure):
+    _fields_ = [("layout", VdiLayout), ("w", C.c_int), ("h", C.c_int), ("n_s", C.c_int), ("colour_fmt", C.c_int),
+                ("grid_tile", C.c_int), ("frame_recorded", C.c_int), ("frame_w", C.c_int), ("frame_h", C.c_int),
+                ("rays_hit", C.c_uint64), ("lists", C.c_uint64), ("pieces", C.c_uint64)]
 
 
 class VdiVolume(C.Structure):
@@ -105,7 +111,8 @@ class VdiServerCounters(C.Structure):
 
 class VdiRenderOpts(C.Structure):
     _fields_ = [("search", C.c_int), ("no_ert", C.c_int), ("ray_lists", C.c_void_p),
-                ("ray_segs", C.c_void_p), ("warp_shape", C.c_int), ("ess", C.c_int), ("blocks", C.c_int)]
+                ("ray_segs", C.c_void_p), ("warp_shape", C.c_int), ("ess", C.c_int), ("blocks", C.c_int),
+                ("record_stats", C.c_int)]
 
 
 _lib = None
@@ -138,6 +145,7 @@ def load(build_if_needed: bool = True):
     _sig(L, "vdi_create", [P, P, P, P, P, C.c_int, P, C.POINTER(P)])
     _sig(L, "vdi_download", [P, P, P, P, P, P])
     _sig(L, "vdi_get_layout", [P, P])
+    _sig(L, "vdi_stats", [P, P, P])
     _sig(L, "vdi_destroy", [P], None)
     _sig(L, "vdi_render", [P, P, C.c_int, C.c_int, C.c_int, C.c_int, P, C.c_int, P])
     _sig(L, "vdi_render_ex", [P, P, C.c_int, C.c_int, C.c_int, C.c_int, P, C.c_int, P, P])
@@ -256,6 +264,13 @@ def vdi_create(ctx, d: VdiDesc, rgba, depth, counts=None, stream=None):
     return out
 
 
+def vdi_stats(vdi, stream=None) -> VdiStats:
+    """Bytes by array, grid shape and the last counted frame's totals (synchronises ``stream``)."""
+    out = VdiStats()
+    _check(load().vdi_stats(vdi, C.byref(out), _stream(stream)))
+    return out
+
+
 def vdi_get_layout(vdi) -> VdiLayout:
     out = VdiLayout()
     _check(load().vdi_get_layout(vdi, C.byref(out)))
@@ -291,10 +306,10 @@ def vdi_render_preview_static(vdi, cam: VdiCamera, W, H, d_i, d_r, out, out_fmt=
 
 def vdi_render_ex(vdi, cam: VdiCamera, W, H, d_i, d_r, out, out_fmt=VDI_F32, search=VDI_SEARCH_ALG2,
                   no_ert=False, ray_lists=None, ray_segs=None, warp_shape=-1, ess=False, blocks=False,
-                  stream=None):
+                  record_stats=False, stream=None):
     o = VdiRenderOpts()
     o.search, o.no_ert, o.warp_shape, o.ess = int(search), int(bool(no_ert)), int(warp_shape), int(bool(ess))
-    o.blocks = int(bool(blocks))
+    o.blocks, o.record_stats = int(bool(blocks)), int(bool(record_stats))
     o.ray_lists, o.ray_segs = _dptr(ray_lists), _dptr(ray_segs)
     _check(load().vdi_render_ex(vdi, C.byref(cam), int(W), int(H), int(d_i), int(d_r), _dptr(out),
                                 int(out_fmt), C.byref(o), _stream(stream)))
@@ -406,7 +421,7 @@ class PiController:
 
 
 def vdi_touch_bitmap(vdi, cam: VdiCamera, W, H, bitmap, stream=None):
-    """bitmap: zeroed int32 CUDA tensor with >= ceil((depth_bytes + colour_bytes) / 128) elements."""
+    """bitmap: zeroed int32 CUDA tensor of at least the length touched_bytes() allocates (see vdi.h)."""
     _check(load().vdi_touch_bitmap(vdi, C.byref(cam), int(W), int(H), _dptr(bitmap), int(bitmap.numel()),
                                    _stream(stream)))
 

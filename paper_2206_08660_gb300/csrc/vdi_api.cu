@@ -33,6 +33,8 @@ cudaError_t launch_range(const float *depth, const int32_t *counts, int ns, long
                          cudaStream_t st);
 cudaError_t launch_download(const DevVdi &v, int ns, float *rgba, float *depth, int32_t *counts,
                             cudaStream_t st);
+cudaError_t launch_count_totals(const uint32_t *lists, const uint32_t *segs, long long n, unsigned long long *totals,
+                                int sm_count, cudaStream_t st);
 
 static thread_local char g_err[512];
 
@@ -512,6 +514,7 @@ void free_vdi(vdi_t *v) {
     if (v->colour_mem) cudaFreeAsync(v->colour_mem, fs);
     if (v->grid_mem) cudaFreeAsync(v->grid_mem, fs);
     if (v->range_mem) cudaFreeAsync(v->range_mem, fs);
+    if (v->totals_mem) cudaFreeAsync(v->totals_mem, fs);
     delete v;
 }
 
@@ -633,10 +636,11 @@ VDI_API vdi_status vdi_render_ex(vdi_t *v, const vdi_camera *view, int W, int H,
                                  void *out_rgba, int out_fmt, const vdi_render_opts *opts, void *stream) {
     vdi_status st_ = check_render_args(v, W, H, d_i, d_r, out_rgba, out_fmt);
     if (st_ != VDI_OK) return st_;
-    vdi_render_opts o = {VDI_SEARCH_ALG2, 0, nullptr, nullptr, -1, 0, 0};
+    vdi_render_opts o = {VDI_SEARCH_ALG2, 0, nullptr, nullptr, -1, 0, 0, 0};
     if (opts) o = *opts;
     if (o.search < 0 || o.search > 2) return fail(VDI_ERR_INVALID_ARG, "search=%d", o.search);
     if (o.warp_shape < -1 || o.warp_shape > 3) return fail(VDI_ERR_INVALID_ARG, "warp_shape=%d", o.warp_shape);
+    if (o.record_stats && d_r != 1) return fail(VDI_ERR_UNSUPPORTED, "frame totals are counted on exact renders (d_r = 1)");
     cudaSetDevice(v->ctx->device);
     cudaStream_t st = (cudaStream_t)stream;
     const int Wr = div_up(W, d_i), Hr = div_up(H, d_i);
@@ -645,6 +649,17 @@ VDI_API vdi_status vdi_render_ex(vdi_t *v, const vdi_camera *view, int W, int H,
     if (st_ != VDI_OK) return st_;
     const int ws = o.warp_shape >= 0 ? o.warp_shape : default_warp_shape(c);
     float4 *lo = nullptr;
+    uint32_t *tmp_counters = nullptr;
+    if (o.record_stats) {
+        // per-ray counters (the caller's, or temporary ones) summed into the VDI's totals
+        if (!v->totals_mem) CK(cudaMallocAsync((void **)&v->totals_mem, 3 * sizeof(unsigned long long), st));
+        if (!o.ray_lists || !o.ray_segs) {
+            CK(cudaMallocAsync((void **)&tmp_counters, 2 * (size_t)Wr * Hr * sizeof(uint32_t), st));
+            if (!o.ray_lists) o.ray_lists = tmp_counters;
+            if (!o.ray_segs) o.ray_segs = tmp_counters + (size_t)Wr * Hr;
+        }
+        CK(cudaMemsetAsync(v->totals_mem, 0, 3 * sizeof(unsigned long long), st));
+    }
     if (d_i == 1) {
         CK(launch_render(c, v->dv, out_rgba, out_fmt, o.ray_lists, o.ray_segs, o.search, ws, !o.no_ert, o.ess != 0, o.blocks != 0, st));
     } else {
@@ -652,8 +667,15 @@ VDI_API vdi_status vdi_render_ex(vdi_t *v, const vdi_camera *view, int W, int H,
         CK(launch_render(c, v->dv, lo, VDI_F32, o.ray_lists, o.ray_segs, o.search, ws, !o.no_ert, o.ess != 0, o.blocks != 0, st));
         CK(launch_upsample(lo, Wr, Hr, out_rgba, out_fmt, W, H, st));
     }
+    if (o.record_stats) {
+        CK(launch_count_totals(o.ray_lists, o.ray_segs, (long long)Wr * Hr, v->totals_mem, v->ctx->sm_count, st));
+        v->frame_recorded = 1;
+        v->frame_w = Wr;
+        v->frame_h = Hr;
+    }
 done:
     if (lo) cudaFreeAsync(lo, st);
+    if (tmp_counters) cudaFreeAsync(tmp_counters, st);
     return st_;
 }
 
@@ -679,6 +701,33 @@ VDI_API vdi_status vdi_render_scaled(vdi_t *v, const vdi_camera *view, int W, in
 done:
     if (lo) cudaFreeAsync(lo, st);
     return st_;
+}
+
+VDI_API vdi_status vdi_stats(vdi_t *v, vdi_stats_t *out, void *stream) {
+    if (!v || !out) return fail(VDI_ERR_INVALID_ARG, "NULL argument");
+    vdi_stats_t s{};
+    s.layout = v->layout;
+    s.w = v->desc.w;
+    s.h = v->desc.h;
+    s.n_s = v->desc.n_s;
+    s.colour_fmt = v->desc.colour_fmt;
+    s.grid_tile = v->desc.grid_tile;
+    if (v->frame_recorded && v->totals_mem) {
+        cudaSetDevice(v->ctx->device);
+        unsigned long long t[3] = {0, 0, 0};
+        cudaStream_t st = (cudaStream_t)stream;
+        cudaError_t e = cudaMemcpyAsync(t, v->totals_mem, sizeof t, cudaMemcpyDeviceToHost, st);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+        if (e != cudaSuccess) return cuda_fail(e, "reading frame totals");
+        s.frame_recorded = 1;
+        s.frame_w = v->frame_w;
+        s.frame_h = v->frame_h;
+        s.rays_hit = t[0];
+        s.lists = t[1];
+        s.pieces = t[2];
+    }
+    *out = s;
+    return VDI_OK;
 }
 
 VDI_API vdi_status vdi_render(vdi_t *v, const vdi_camera *view, int W, int H, int d_i, int d_r, void *out_rgba,

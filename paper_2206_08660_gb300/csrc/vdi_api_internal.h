@@ -25,6 +25,9 @@ struct vdi_t {
     uint32_t *grid_mem = nullptr;
     float2 *range_mem = nullptr;
     float2 *brange_mem = nullptr;
+    // frame totals of the last counted render (vdi_stats): rays hit, lists, pieces
+    unsigned long long *totals_mem = nullptr;
+    int frame_recorded = 0, frame_w = 0, frame_h = 0;
 };
 
 namespace vdi {

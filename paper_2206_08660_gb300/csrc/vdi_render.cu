@@ -13,6 +13,8 @@
 #include <math.h>
 #include <stdint.h>
 
+#include <algorithm>
+
 #include "vdi_internal.cuh"
 #include "vdi_march.cuh"
 
@@ -145,6 +147,37 @@ __global__ void search_kernel(const DevVdi v, int li, const float *d_entry, cons
         if (j >= 0 && ld_back(v, j, li) < dx) j = -1;
     }
     result[q] = j;
+}
+
+// Frame totals from per-ray counters: rays with at least one list, lists and
+// pieces summed over the n rays (one atomic add per warp and total).
+__global__ void count_totals_kernel(const uint32_t *__restrict__ lists, const uint32_t *__restrict__ segs, long long n,
+                                    unsigned long long *totals) {
+    unsigned long long hit = 0, nl = 0, ns = 0;
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+        const uint32_t l = lists[i];
+        hit += l > 0;
+        nl += l;
+        ns += segs[i];
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        hit += __shfl_down_sync(0xffffffffu, hit, o);
+        nl += __shfl_down_sync(0xffffffffu, nl, o);
+        ns += __shfl_down_sync(0xffffffffu, ns, o);
+    }
+    if ((threadIdx.x & 31) == 0) {
+        atomicAdd(totals + 0, hit);
+        atomicAdd(totals + 1, nl);
+        atomicAdd(totals + 2, ns);
+    }
+}
+
+cudaError_t launch_count_totals(const uint32_t *lists, const uint32_t *segs, long long n, unsigned long long *totals,
+                                int sm_count, cudaStream_t st) {
+    const int blocks = (int)std::min<long long>(div_up((int)std::min<long long>(n, 1LL << 30), 256), 4LL * sm_count);
+    count_totals_kernel<<<std::max(blocks, 1), 256, 0, st>>>(lists, segs, n, totals);
+    return cudaGetLastError();
 }
 
 // ---------------------------------------------------------------------------

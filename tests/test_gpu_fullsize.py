@@ -20,7 +20,8 @@ import pytest
 
 import bench as B
 import vdi_synth as S
-from helpers import check_tolerance
+from helpers import check_tolerance, check_with_alternatives, closest_alternative, exact_alternatives, \
+    preview_alternatives
 
 pytestmark = pytest.mark.gpu
 torch = pytest.importorskip("torch")
@@ -63,17 +64,31 @@ def gpu_frame(V, vdi, cam, W, H, d_i, d_r):
     return out.float().cpu().numpy().reshape(-1, 4)
 
 
-def oracle_frame(orc, sc, cam, W, H, d_i, d_r):
+def check_frame(V, orc, sc, vdi, cam, W, H, d_i, d_r, got, fmt, what):
+    """A frame against the oracle.  Flagged rays match one of the oracle's limits
+    (nudged pixel centres for the exact path, flipped tie decisions for D_R);
+    with D_I the GPU's low-resolution image is checked ray by ray first, then
+    the whole upsampled frame against the oracle's upsampling of its limits."""
     Wr, Hr = -(-W // d_i), -(-H // d_i)
     if d_r == 1:
-        lo, fl = orc.render_exact(sc, cam.view, cam.proj, Wr, Hr)[0], np.zeros(Wr * Hr, np.uint8)
+        lo, _, _, fl = orc.render_exact(sc, cam.view, cam.proj, Wr, Hr)
+        idx = np.nonzero(fl)[0]
+        alts = exact_alternatives(orc, sc, cam, Wr, Hr, idx)[0] if len(idx) else np.zeros((1, 0, 4))
     else:
-        lo, fl = orc.render_preview(sc, cam.view, cam.proj, Wr, Hr, d_r)
+        grid = orc.grid_counts(sc, 8, 20)
+        lo, fl = orc.render_preview(sc, cam.view, cam.proj, Wr, Hr, d_r, 8, 20, grid=grid)
+        idx = np.nonzero(fl)[0]
+        alts = preview_alternatives(orc, sc, cam, Wr, Hr, d_r, 8, 20, grid, idx)
+    assert lo[:, 3].max() > 0.5
     if d_i == 1:
-        return lo, fl == 0
-    hi = orc.upsample(lo, Wr, Hr, W, H)
-    touched = orc.upsample(np.repeat(fl.astype(np.float64)[:, None], 4, 1), Wr, Hr, W, H)[:, 0] > 0
-    return hi, ~touched
+        return check_with_alternatives(got, lo, fmt, fl, alts, what=what)
+    got_lo = gpu_frame(V, vdi, cam, Wr, Hr, 1, d_r)
+    frac = check_with_alternatives(got_lo, lo, fmt, fl, alts, what=what + " low-res")
+    lo = lo.copy()
+    if len(idx):
+        lo[idx] = closest_alternative(got_lo[idx], alts)
+    check_tolerance(got, orc.upsample(lo, Wr, Hr, W, H), fmt, what=what)
+    return frac
 
 
 def test_large_workload_benchmark_frames(V, ctx, orc):
@@ -91,9 +106,8 @@ def test_large_workload_benchmark_frames(V, ctx, orc):
             if az == 20.0:
                 continue  # 10 and 30 degrees bracket it; keeps the test short
             got = gpu_frame(V, vdi, cn, wl["W"], wl["H"], d_i, d_r)
-            ref, ok = oracle_frame(orc, sc, cn, wl["W"], wl["H"], d_i, d_r)
-            assert ok.mean() > 0.8 and ref[:, 3].max() > 0.5
-            check_tolerance(got, ref, 1, mask=ok, what=f"large {az} deg D_I={d_i} D_R={d_r}")
+            check_frame(V, orc, sc, vdi, cn, wl["W"], wl["H"], d_i, d_r, got, 1,
+                        what=f"large {az} deg D_I={d_i} D_R={d_r}")
     finally:
         V.vdi_destroy(vdi)
 
@@ -107,10 +121,8 @@ def test_plain_workload_views(V, ctx, orc):
     try:
         for (az, d_i, d_r), cn in zip(wl["frames"], views):
             got = gpu_frame(V, vdi, cn, wl["W"], wl["H"], d_i, d_r)
-            ref, ok = oracle_frame(orc, sc, cn, wl["W"], wl["H"], d_i, d_r)
-            assert ref[:, 3].max() > 0.5
             # FP16 output rounding (<= 2.5e-4) sits well inside the FP32 tolerance
-            check_tolerance(got, ref, 0, what=f"plain {az} deg")
+            check_frame(V, orc, sc, vdi, cn, wl["W"], wl["H"], d_i, d_r, got, 0, what=f"plain {az} deg")
     finally:
         V.vdi_destroy(vdi)
 
