@@ -227,7 +227,9 @@ class OracleLeg:
         measured = full = 0.0
         for (az, d_i, d_r), cn in zip(self.wl["frames"], self.views):
             Wr, Hr = -(-self.wl["W"] // d_i), -(-self.wl["H"] // d_i)
-            pix = rng.integers(0, Wr * Hr, size=min(R, Wr * Hr)).astype(np.int32)
+            # a whole frame when the sample would hold as many rays, else a random sample
+            pix = None if R >= Wr * Hr else rng.integers(0, Wr * Hr, size=R).astype(np.int32)
+            n = Wr * Hr if pix is None else len(pix)
             t = time.perf_counter()
             if d_r == 1:
                 self.o.render_exact(self.sc, cn.view, cn.proj, Wr, Hr, pix=pix, nthreads=self.threads)
@@ -236,25 +238,30 @@ class OracleLeg:
                                       nthreads=self.threads)
             dt = time.perf_counter() - t
             measured += dt
-            full += dt / len(pix) * (Wr * Hr)
+            full += dt / n * (Wr * Hr)
         return measured, full
 
     def rays_for_budget(self, budget_s, rng, probe=2048):
         """Rays per frame so that one run() takes about budget_s seconds."""
         self.run(256, rng)  # first touch of the scene and thread start-up, untimed
         m, _ = self.run(probe, rng)
-        return int(min(400000, max(probe, probe * budget_s / max(m, 1e-6))))
+        return int(max(probe, probe * budget_s / max(m, 1e-6)))
 
     def rays_per_step(self):
         """Rays of one whole step (every frame at its rendered resolution)."""
         return sum((-(-self.wl["W"] // d_i)) * (-(-self.wl["H"] // d_i)) for (_, d_i, _) in self.wl["frames"])
 
     def sample_text(self, R):
-        counts = sorted({min(R, (-(-self.wl["W"] // d_i)) * (-(-self.wl["H"] // d_i)))
-                         for (_, d_i, _) in self.wl["frames"]})
+        sizes = [(-(-self.wl["W"] // d_i)) * (-(-self.wl["H"] // d_i)) for (_, d_i, _) in self.wl["frames"]]
+        if all(R >= s for s in sizes):
+            return (f"whole frames: all {len(self.wl['frames'])} frames of the step at their full ray counts "
+                    f"({'/'.join(str(s) for s in sorted(set(sizes)))}); oracle VDI from the oracle's own FP32 "
+                    f"generation, count grid built once")
+        counts = sorted({min(R, s) for s in sizes})
         n = str(counts[0]) if len(counts) == 1 else "/".join(str(c) for c in counts)
-        return (f"{n} random rays (drawn with repetition) from each of the {len(self.wl['frames'])} frames per step, "
-                f"timed and extrapolated to full frames; oracle VDI from the oracle's own FP32 generation")
+        return (f"{n} rays from each of the {len(self.wl['frames'])} frames per step (a whole frame where the "
+                f"sample reaches its ray count, else drawn at random with repetition), extrapolated to full frames; "
+                f"oracle VDI from the oracle's own FP32 generation, count grid built once")
 
 
 SERVING = dict(n_vdis=8, w=1920, h=1080, ns=24, tau=0.01, vol_n=512, rate=240.0, seconds=8.0, replace_every=2.0,

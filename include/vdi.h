@@ -310,15 +310,23 @@ vdi_status vdi_autotune_batch(vdi_ctx *ctx, const vdi_request *reqs, int n, void
  *  - a scheduler thread admits queued requests FIFO into the next batch as
  *    soon as one of `max_inflight` batch streams is free and their image
  *    memory (plus low-resolution scratch for D_I > 1) fits under
- *    `budget_bytes` next to everything not yet released; a request that can
- *    never fit fails with VDI_ERR_OOM; batches run while new requests are
- *    admitted behind them (continuous batching, work overlaps on the device);
+ *    `budget_bytes` next to everything not yet released and the resident
+ *    VDIs; a request that can never fit fails with VDI_ERR_OOM; batches run
+ *    while new requests are admitted behind them (continuous batching, work
+ *    overlaps on the device);
  *  - each batch is one vdi_render_batch launch: every result equals the same
  *    view rendered alone by vdi_render;
  *  - vdi_server_set_vdi installs or replaces a slot's VDI at any time (the
  *    server takes ownership).  Batches formed after the work enqueued on
  *    `ready_stream` (e.g. the side stream of a vdi_generate) has completed use
  *    the new VDI; the old one is freed when the last batch using it retires;
+ *  - the budget is a device budget: every live VDI version (layout
+ *    total_bytes; a replaced one until its last batch retires) counts against
+ *    it next to images and scratch.  vdi_server_set_vdi returns VDI_ERR_OOM
+ *    (the caller keeps the VDI) when the VDI does not fit;
+ *    vdi_server_generate charges the new VDI's bytes before generating it
+ *    (vdi_generate on `stream`, then an install ready on that stream) and
+ *    returns VDI_ERR_OOM without generating when they do not fit;
  *  - results stay in server-owned DEVICE memory until vdi_server_release;
  *  - waits are bounded: vdi_server_wait returns VDI_ERR_TIMEOUT;
  *  - batches run on streams of the highest priority, so work the caller
@@ -327,7 +335,7 @@ vdi_status vdi_autotune_batch(vdi_ctx *ctx, const vdi_request *reqs, int n, void
 typedef struct vdi_server vdi_server;
 
 typedef struct {
-    size_t budget_bytes;   /* device memory for unreleased results and preview scratch */
+    size_t budget_bytes;   /* device memory for resident VDIs, unreleased results and preview scratch */
     int max_batch;         /* requests per launch, 1..VDI_BATCH_MAX_REQUESTS */
     int max_inflight;      /* batches on the device at once (streams), 1..16 */
     int n_slots;           /* resident VDI slots, 1..VDI_BATCH_MAX_VDIS */
@@ -353,11 +361,14 @@ typedef struct {
 typedef struct {
     uint64_t submitted, completed, failed, batches, batched_requests, vdi_installs;
     uint64_t pending, batches_in_flight;
-    size_t bytes_in_use;
+    size_t bytes_in_use;   /* unreleased images and preview scratch */
+    size_t vdi_bytes;      /* live VDI versions and VDIs being generated through the server */
 } vdi_server_counters;
 
 vdi_status vdi_server_create(vdi_ctx *ctx, const vdi_server_config *cfg, vdi_server **out);
 vdi_status vdi_server_set_vdi(vdi_server *s, int slot, vdi_t *vdi, void *ready_stream);
+/* vdi_server_generate (after vdi_generate below): generation into a slot, its
+ * bytes charged to the budget first. */
 vdi_status vdi_server_submit(vdi_server *s, const vdi_view_request *req, uint64_t *ticket);
 vdi_status vdi_server_wait(vdi_server *s, uint64_t ticket, double timeout_s, vdi_ticket_info *info);
 vdi_status vdi_server_poll(vdi_server *s, uint64_t ticket, vdi_ticket_info *info);
@@ -421,6 +432,15 @@ typedef struct {
 
 vdi_status vdi_generate(vdi_ctx *ctx, const vdi_volume *vol, const vdi_tf *tf, const vdi_gen_params *params,
                         void *stream, vdi_t **out);
+
+/* Serving (above): generate a VDI on `stream` (vdi_generate of the server's
+ * context) and install it in `slot` once that stream reaches the end of the
+ * generation, with its device bytes (vdi_layout_bytes of the parameters)
+ * charged to the server's budget before anything is allocated.  VDI_ERR_OOM
+ * when they do not fit next to the resident VDIs and unreleased results;
+ * other errors as vdi_generate.  Returns after enqueueing. */
+vdi_status vdi_server_generate(vdi_server *s, int slot, const vdi_volume *vol, const vdi_tf *tf,
+                               const vdi_gen_params *params, void *stream);
 
 /* ---- ground truth and image quality (Section 6) ----------------------------
  * vdi_dvr: direct volume rendering of the volume from `view` (an OpenGL

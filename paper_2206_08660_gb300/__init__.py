@@ -22,7 +22,7 @@ __all__ = [
     "VDI_SEARCH_LINEAR", "VdiError", "VdiCamera", "VdiDesc", "VdiLayout", "VdiRenderOpts", "load",
     "vdi_ctx_create", "vdi_ctx_destroy", "vdi_layout_bytes", "vdi_create", "vdi_download", "vdi_get_layout", "vdi_stats",
     "vdi_destroy", "vdi_render", "vdi_render_ex", "vdi_render_preview_static", "VDI_STATIC_PREVIEW_PIXELS", "vdi_search_first", "vdi_generate", "vdi_touch_bitmap", "vdi_render_batch", "vdi_autotune_batch", "request",
-    "vdi_server_create", "vdi_server_set_vdi", "vdi_server_submit", "vdi_server_wait", "vdi_server_poll",
+    "vdi_server_create", "vdi_server_set_vdi", "vdi_server_generate", "vdi_server_submit", "vdi_server_wait", "vdi_server_poll",
     "vdi_server_release", "vdi_server_read", "vdi_server_stats", "vdi_server_destroy", "VdiViewRequest", "VdiTicketInfo",
     "VdiRequest", "VdiBatchOpts", "camera", "desc",
 ]
@@ -106,7 +106,8 @@ class VdiTicketInfo(C.Structure):
 class VdiServerCounters(C.Structure):
     _fields_ = [("submitted", C.c_uint64), ("completed", C.c_uint64), ("failed", C.c_uint64),
                 ("batches", C.c_uint64), ("batched_requests", C.c_uint64), ("vdi_installs", C.c_uint64),
-                ("pending", C.c_uint64), ("batches_in_flight", C.c_uint64), ("bytes_in_use", C.c_size_t)]
+                ("pending", C.c_uint64), ("batches_in_flight", C.c_uint64), ("bytes_in_use", C.c_size_t),
+                ("vdi_bytes", C.c_size_t)]
 
 
 class VdiRenderOpts(C.Structure):
@@ -163,6 +164,7 @@ def load(build_if_needed: bool = True):
     _sig(L, "vdi_autotune_batch", [P, P, C.c_int, P, P, P])
     _sig(L, "vdi_server_create", [P, P, C.POINTER(P)])
     _sig(L, "vdi_server_set_vdi", [P, C.c_int, P, P])
+    _sig(L, "vdi_server_generate", [P, C.c_int, P, P, P, P])
     _sig(L, "vdi_server_submit", [P, P, C.POINTER(C.c_uint64)])
     _sig(L, "vdi_server_wait", [P, C.c_uint64, C.c_double, P])
     _sig(L, "vdi_server_poll", [P, C.c_uint64, P])
@@ -481,8 +483,22 @@ def vdi_server_create(ctx, budget_bytes, max_batch=32, max_inflight=2, n_slots=8
 
 
 def vdi_server_set_vdi(server, slot, vdi, ready_stream=None):
-    """Install or replace the VDI of a slot; the server takes ownership of `vdi`."""
+    """Install or replace the VDI of a slot; the server takes ownership of `vdi`
+    (on VDI_ERR_OOM the caller keeps it)."""
     _check(load().vdi_server_set_vdi(server, int(slot), vdi, _stream(ready_stream)))
+
+
+def vdi_server_generate(server, slot, volume, bbox_min, bbox_max, knots, cam_o: VdiCamera, w, h, n_s, tau, step,
+                        length_unit, colour_fmt=VDI_F32, grid_tile=0, grid_nz=0, stream=None, adaptive=False):
+    """vdi_generate into a slot of the server, its bytes charged to the budget first."""
+    vol, tf, kn = _volume_tf(volume, bbox_min, bbox_max, knots)
+    p = VdiGenParams()
+    p.w, p.h, p.n_s, p.orig = int(w), int(h), int(n_s), cam_o
+    p.tau, p.step, p.length_unit = float(tau), float(step), float(length_unit)
+    p.colour_fmt, p.grid_tile, p.grid_nz = int(colour_fmt), int(grid_tile), int(grid_nz)
+    p.adaptive = 1 if adaptive else 0
+    _check(load().vdi_server_generate(server, int(slot), C.byref(vol), C.byref(tf), C.byref(p), _stream(stream)))
+    del kn
 
 
 def view_request(slot, cam: VdiCamera, W, H, d_i=1, d_r=1, out_fmt=VDI_F16, Wr=0, Hr=0) -> VdiViewRequest:

@@ -12,9 +12,14 @@
 //  - a VDI slot can be replaced at any time: the new VDI is used by batches
 //    formed after its producer stream has reached the replacement point, and
 //    the old one is freed once no in-flight batch references it;
-//  - every wait is bounded (VDI_ERR_TIMEOUT), errors land on the ticket.
+//  - every wait is bounded (VDI_ERR_TIMEOUT), errors land on the ticket;
+//  - the memory budget is a device budget: resident VDI versions (including
+//    a replaced one still read by in-flight batches) and a VDI being
+//    generated through the server are charged next to images and scratch.
 // One scheduler thread owns all CUDA work of the server.
 #include <cuda_runtime.h>
+
+#include <atomic>
 #include <math.h>
 #include <stdint.h>
 #include <string.h>
@@ -44,9 +49,12 @@ struct VdiVersion {  // one VDI installed in a slot, shared by the batches that 
     vdi_t *vdi = nullptr;
     cudaEvent_t ready = nullptr;  // recorded on the producer stream at install time
     bool ready_seen = false;
+    std::atomic<size_t> *charge = nullptr;  // the server's resident-VDI bytes, while this version lives
+    size_t bytes = 0;
     ~VdiVersion() {
         if (ready) cudaEventDestroy(ready);
         if (vdi) free_vdi(vdi);
+        if (charge) charge->fetch_sub(bytes);
     }
 };
 
@@ -78,6 +86,10 @@ struct vdi_server {
     std::condition_variable done_cv;  // wakes waiters
     std::deque<uint64_t> pending;
     std::unordered_map<uint64_t, vdi::Ticket> tickets;
+    // device bytes of the live VDI versions (declared before the slots and
+    // batches that hold versions, so it outlives them)
+    std::atomic<size_t> vdi_bytes{0};
+    size_t reserved = 0;  // bytes held for VDIs being generated through the server
     std::vector<std::shared_ptr<vdi::VdiVersion>> slots;
     std::vector<vdi::Batch> batches;
     uint64_t next_ticket = 1;
@@ -163,12 +175,19 @@ static bool launch_one(vdi_server *s) {
             continue;
         }
         const size_t need = request_bytes(r);
-        if (need > s->cfg.budget_bytes) {  // can never fit: reject instead of blocking the queue
+        const size_t held = s->vdi_bytes.load() + s->reserved;  // resident and incoming VDIs
+        bool idle = true;  // nothing in flight or unreleased that could free memory later
+        for (auto &b : s->batches) idle &= !b.busy;
+        idle &= s->used == 0;
+        if (need > s->cfg.budget_bytes || (idle && held + need > s->cfg.budget_bytes)) {
+            // can never fit (or not while these VDIs stay resident and nothing else runs):
+            // reject instead of blocking the queue
             s->pending.pop_front();
+            fail(VDI_ERR_OOM, "request needs %zu bytes; budget %zu, VDIs hold %zu", need, s->cfg.budget_bytes, held);
             finish(s, id, VDI_ERR_OOM);
             continue;
         }
-        if (s->used + need > s->cfg.budget_bytes) break;  // admission by memory: wait for releases
+        if (s->used + held + need > s->cfg.budget_bytes) break;  // admission by memory: wait for releases
         std::shared_ptr<VdiVersion> ver = s->slots[r.slot];
         if (!ver->ready_seen) {
             const cudaError_t q = cudaEventQuery(ver->ready);
@@ -284,26 +303,88 @@ VDI_API vdi_status vdi_server_create(vdi_ctx *ctx, const vdi_server_config *cfg,
     return VDI_OK;
 }
 
-VDI_API vdi_status vdi_server_set_vdi(vdi_server *s, int slot, vdi_t *vdi, void *ready_stream) {
-    if (!s || !vdi) return fail(VDI_ERR_INVALID_ARG, "NULL argument");
-    if (slot < 0 || slot >= (int)s->slots.size()) return fail(VDI_ERR_INVALID_ARG, "slot %d", slot);
-    if (vdi->ctx != s->ctx) return fail(VDI_ERR_INVALID_ARG, "VDI of another context");
+// Bytes the live VDIs would hold after installing `incoming` bytes in `slot`:
+// the slot's current version is freed at once when nothing but the slot
+// holds it, else it lives until its last batch retires.  Lock held.
+static size_t vdi_bytes_after_install(vdi_server *s, int slot, size_t incoming) {
+    size_t b = s->vdi_bytes.load() + incoming;
+    const auto &old = s->slots[slot];
+    if (old && old.use_count() == 1) b -= old->bytes;
+    return b;
+}
+
+// Install `vdi` in `slot` with its ready event on `ready_stream`; `reserved`
+// bytes held for it (by vdi_server_generate) convert into its charge.
+static vdi_status install(vdi_server *s, int slot, vdi_t *vdi, cudaStream_t ready_stream, size_t reserved) {
     cudaSetDevice(s->ctx->device);
     auto ver = std::make_shared<VdiVersion>();
     cudaError_t e = cudaEventCreateWithFlags(&ver->ready, cudaEventDisableTiming);
-    if (e == cudaSuccess) e = cudaEventRecord(ver->ready, (cudaStream_t)ready_stream);
-    if (e != cudaSuccess) {
-        ver->vdi = nullptr;  // the caller keeps ownership when the install fails
-        return cuda_fail(e, "set_vdi");
-    }
-    ver->vdi = vdi;
+    if (e == cudaSuccess) e = cudaEventRecord(ver->ready, ready_stream);
+    if (e != cudaSuccess) return cuda_fail(e, "set_vdi");  // ver->vdi is still null: the caller keeps the VDI
+    const size_t bytes = vdi->layout.total_bytes;
     {
         std::lock_guard<std::mutex> g(s->mu);
+        s->reserved -= reserved;
+        if (s->used + s->reserved + vdi_bytes_after_install(s, slot, bytes) > s->cfg.budget_bytes) {
+            s->cv.notify_all();
+            return fail(VDI_ERR_OOM, "VDI of %zu bytes does not fit the budget of %zu next to %zu in use", bytes,
+                        s->cfg.budget_bytes, s->used + s->reserved + s->vdi_bytes.load());
+        }
+        ver->vdi = vdi;
+        ver->bytes = bytes;
+        ver->charge = &s->vdi_bytes;
+        s->vdi_bytes.fetch_add(bytes);
         s->slots[slot] = ver;  // the previous version dies with the last batch holding it
         s->st.vdi_installs++;
     }
     s->cv.notify_all();
     return VDI_OK;
+}
+
+VDI_API vdi_status vdi_server_set_vdi(vdi_server *s, int slot, vdi_t *vdi, void *ready_stream) {
+    if (!s || !vdi) return fail(VDI_ERR_INVALID_ARG, "NULL argument");
+    if (slot < 0 || slot >= (int)s->slots.size()) return fail(VDI_ERR_INVALID_ARG, "slot %d", slot);
+    if (vdi->ctx != s->ctx) return fail(VDI_ERR_INVALID_ARG, "VDI of another context");
+    return install(s, slot, vdi, (cudaStream_t)ready_stream, 0);
+}
+
+VDI_API vdi_status vdi_server_generate(vdi_server *s, int slot, const vdi_volume *vol, const vdi_tf *tf,
+                                       const vdi_gen_params *params, void *stream) {
+    if (!s || !vol || !tf || !params) return fail(VDI_ERR_INVALID_ARG, "NULL argument");
+    if (slot < 0 || slot >= (int)s->slots.size()) return fail(VDI_ERR_INVALID_ARG, "slot %d", slot);
+    vdi_desc d{};
+    d.w = params->w;
+    d.h = params->h;
+    d.n_s = params->n_s;
+    d.orig = params->orig;
+    for (int k = 0; k < 3; ++k) {
+        d.bbox_min[k] = vol->bbox_min[k];
+        d.bbox_max[k] = vol->bbox_max[k];
+    }
+    d.length_unit = params->length_unit;
+    d.colour_fmt = params->colour_fmt;
+    d.grid_tile = params->grid_tile;
+    d.grid_nz = params->grid_nz;
+    vdi_layout L;
+    vdi_status st_ = vdi_layout_bytes(&d, &L);
+    if (st_ != VDI_OK) return st_;
+    {  // hold the new VDI's bytes before it is allocated
+        std::lock_guard<std::mutex> g(s->mu);
+        if (s->used + s->reserved + vdi_bytes_after_install(s, slot, L.total_bytes) > s->cfg.budget_bytes)
+            return fail(VDI_ERR_OOM, "generating a VDI of %zu bytes exceeds the budget of %zu next to %zu in use",
+                        L.total_bytes, s->cfg.budget_bytes, s->used + s->reserved + s->vdi_bytes.load());
+        s->reserved += L.total_bytes;
+    }
+    vdi_t *v = nullptr;
+    st_ = vdi_generate(s->ctx, vol, tf, params, stream, &v);
+    if (st_ != VDI_OK) {
+        std::lock_guard<std::mutex> g(s->mu);
+        s->reserved -= L.total_bytes;
+        return st_;
+    }
+    st_ = install(s, slot, v, (cudaStream_t)stream, L.total_bytes);
+    if (st_ != VDI_OK) vdi_destroy(v);
+    return st_;
 }
 
 VDI_API vdi_status vdi_server_submit(vdi_server *s, const vdi_view_request *req, uint64_t *ticket) {
@@ -408,6 +489,7 @@ VDI_API vdi_status vdi_server_stats(vdi_server *s, vdi_server_counters *out) {
     *out = s->st;
     out->pending = s->pending.size();
     out->bytes_in_use = s->used;
+    out->vdi_bytes = s->vdi_bytes.load() + s->reserved;
     int busy = 0;
     for (auto &b : s->batches) busy += b.busy;
     out->batches_in_flight = busy;

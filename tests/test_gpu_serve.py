@@ -7,6 +7,8 @@
 * A slot replaced by a VDI whose producer stream is still busy: its requests
   wait (a bounded wait times out with VDI_ERR_TIMEOUT, then completes).
 * Released results give their memory back.
+* The budget is a device budget: resident VDIs and VDIs generated through the
+  server are charged next to images and scratch.
 """
 import time
 
@@ -176,3 +178,58 @@ def test_preview_controller_session_through_the_server(V, ctx):
     finally:
         V.vdi_server_destroy(srv)
         V.vdi_destroy(ref_vdi)
+
+
+def test_budget_is_a_device_budget(V, ctx):
+    """Resident VDIs count against the server's budget next to images: a VDI
+    that does not fit is refused (the caller keeps it), a request that cannot
+    fit beside the resident VDIs fails at once, and generation through the
+    server charges the new VDI before allocating it (a replacement frees the
+    slot's old VDI when nothing else reads it)."""
+    case, a = make_vdi(V, ctx, 7, 1)
+    _, b = make_vdi(V, ctx, 8, 1)
+    _, c = make_vdi(V, ctx, 9, 1)
+    B = V.vdi_get_layout(a).total_bytes
+    srv = V.vdi_server_create(ctx, budget_bytes=2 * B + (64 << 10), max_batch=4, max_inflight=1, n_slots=3)
+    try:
+        V.vdi_server_set_vdi(srv, 0, a)
+        V.vdi_server_set_vdi(srv, 1, b)
+        assert V.vdi_server_stats(srv).vdi_bytes == 2 * B
+        with pytest.raises(V.VdiError) as e:
+            V.vdi_server_set_vdi(srv, 2, c)
+        assert e.value.status == 2  # VDI_ERR_OOM; the caller still owns c
+        V.vdi_destroy(c)
+        cam = V.camera(case.cam_o.view, case.cam_o.proj)
+        small = V.vdi_server_submit(srv, V.view_request(0, cam, 64, 48, out_fmt=V.VDI_F16))  # 24 KiB
+        assert V.vdi_server_wait(srv, small, 10.0).status == 0
+        V.vdi_server_release(srv, small)
+        # with nothing in flight or unreleased, 512 KiB can never fit beside the two VDIs
+        big = V.vdi_server_submit(srv, V.view_request(0, cam, 256, 256, out_fmt=V.VDI_F16))
+        assert V.vdi_server_wait(srv, big, 10.0).status == 2
+
+        # generation through the server: a 32 x 24 VDI replaces slot 0's 64 x 48 one
+        vol = S.blobs_volume(24, seed=3)
+        bmin, bmax = np.zeros(3), np.ones(3)
+        kn = S.tf_knots("dense")
+        vd = torch.from_numpy(vol).cuda()
+        cam_o = S.orbit_camera(bmin, bmax, 32 / 24, el_deg=15)
+        args = (vd, bmin, bmax, kn, V.camera(cam_o.view, cam_o.proj))
+        side = torch.cuda.Stream()
+        V.vdi_server_generate(srv, 0, *args, 32, 24, 4, 0.02, 1 / 24, 1 / 24, V.VDI_F16, stream=side)
+        direct = V.vdi_generate(ctx, *args, 32, 24, 4, 0.02, 1 / 24, 1 / 24, V.VDI_F16)
+        small_bytes = V.vdi_get_layout(direct).total_bytes
+        assert small_bytes < B and V.vdi_server_stats(srv).vdi_bytes == B + small_bytes
+        cn = S.orbit_camera(bmin, bmax, 1.0, az_deg=20.0, el_deg=15.0)
+        t = V.vdi_server_submit(srv, V.view_request(0, V.camera(cn.view, cn.proj), 48, 48, out_fmt=V.VDI_F16))
+        assert V.vdi_server_wait(srv, t, 20.0).status == 0
+        assert torch.equal(download_image(V, srv, t, 48, 48, 1), alone(V, direct, cn, 48, 48, 1, 1, 1))
+        V.vdi_server_release(srv, t)
+        # a VDI too large for what is left is refused before anything is generated
+        with pytest.raises(V.VdiError) as e:
+            V.vdi_server_generate(srv, 2, *args, 128, 96, 8, 0.02, 1 / 24, 1 / 24, V.VDI_F32, stream=side)
+        assert e.value.status == 2
+        assert V.vdi_server_stats(srv).vdi_bytes == B + small_bytes
+        V.vdi_destroy(direct)
+        torch.cuda.synchronize()
+    finally:
+        V.vdi_server_destroy(srv)
