@@ -24,10 +24,12 @@
 #include "vdi_api_internal.h"
 #include "vdi_internal.cuh"
 #include "vdi_march.cuh"
+#include "vdi_preview.cuh"
 
 namespace vdi {
 
 constexpr int kMaxBatchReq = VDI_BATCH_MAX_REQUESTS;
+constexpr int kBatchLanes = 4;  // lanes per ray of a preview request
 constexpr int kMaxBatchVdi = VDI_BATCH_MAX_VDIS;
 
 struct BatchReq {
@@ -91,27 +93,36 @@ __global__ void __launch_bounds__(256, PREVIEW ? 3 : 4) batch_render_kernel(cons
         const DevVdi &v = P.vdis[q.vdi];
         const int local = tile - q.tile_base;
         const int tx0 = (local % q.tiles_x) * 32, ty0 = (local / q.tiles_x) * 8;
-        int lx, ly;
-        tile_offset<WX>(lx, ly);
-        const int px = tx0 + lx, py = ty0 + ly;
-        if (px < q.c.W && py < q.c.H) {
-            Accum acc = {0.f, 0.f, 0.f, 1.f};
-            uint32_t nl = 0, nsg = 0;
-            Ray ray;
-            if (setup_ray(q.c, px, py, v.w, v.h, ray)) {
-                if (PREVIEW && q.c.d_r > 1) {
-                    if (v.fmt == 0)
-                        march_preview<0, true, 0>(v, q.c, ray, acc);
-                    else
-                        march_preview<1, true, 0>(v, q.c, ray, acc);
-                } else {
+        if (PREVIEW && q.c.d_r > 1) {
+            // a preview tile in kBatchLanes passes of 256 / kBatchLanes rays with
+            // kBatchLanes lanes per ray (the same image as any lane count)
+            const int g = (int)threadIdx.x / kBatchLanes;
+            for (int unit = 0; unit < kBatchLanes; ++unit) {
+                const int px = tx0 + (g & 31), py = ty0 + unit * (8 / kBatchLanes) + (g >> 5);
+                const bool inside = px < q.c.W && py < q.c.H;
+                Ray ray = {};
+                const bool active = inside && setup_ray(q.c, px, py, v.w, v.h, ray);
+                const Accum acc = (v.fmt == 0) ? march_preview_lanes<0, kPreviewProbe, kBatchLanes>(v, q.c, ray, active)
+                                               : march_preview_lanes<1, kPreviewProbe, kBatchLanes>(v, q.c, ray, active);
+                if (inside && (threadIdx.x & (kBatchLanes - 1)) == 0)
+                    store_px(q.out, q.out_fmt, (size_t)py * q.c.W + px, acc);
+            }
+        } else {
+            int lx, ly;
+            tile_offset<WX>(lx, ly);
+            const int px = tx0 + lx, py = ty0 + ly;
+            if (px < q.c.W && py < q.c.H) {
+                Accum acc = {0.f, 0.f, 0.f, 1.f};
+                uint32_t nl = 0, nsg = 0;
+                Ray ray;
+                if (setup_ray(q.c, px, py, v.w, v.h, ray)) {
                     if (v.fmt == 0)
                         march_exact<0, kSearchAlg2, true>(v, ray, acc, nl, nsg);
                     else
                         march_exact<1, kSearchAlg2, true>(v, ray, acc, nl, nsg);
                 }
+                store_px(q.out, q.out_fmt, (size_t)py * q.c.W + px, acc);
             }
-            store_px(q.out, q.out_fmt, (size_t)py * q.c.W + px, acc);
         }
         __syncthreads();  // every thread has read s_tile / s_req before thread 0 writes them again
     }

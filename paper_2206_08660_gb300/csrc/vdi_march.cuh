@@ -606,138 +606,6 @@ __device__ __forceinline__ void march_exact_ess(const DevVdi &v, Ray &r, Accum &
     }
 }
 
-// ---------------------------------------------------------------------------
-// Ray-subsampled preview (Section 4.4): walk the cells of the count grid; in a
-// cell holding c supersegments over F lists, crossed over world length l_c,
-// place n = ceil((c / F) (l_c / cell_depth) / D_R) samples at equal spacing,
-// look each one up in its list (Algorithm 2 search, seeded by the previous
-// sample) and composite with opacity corrected by the spacing.
-// ---------------------------------------------------------------------------
-// PW: depth records requested at once when a sample looks for its
-// supersegment (0: Algorithm 2 with the index carried between samples).  Preview samples lie far apart along the ray, so the index
-// carried from the previous sample seldom helps and Algorithm 2's dependent
-// probes would each cost a memory round trip; instead the list's depth
-// records are read PW pairs at a time and the first slot whose back is at or
-// beyond the sample's depth is picked (the same result as Algorithm 2).  A
-// wide probe suits launches with few rays, a narrow one (fewer registers,
-// more resident warps) launches with many.
-template <int FMT, bool ERT, int PW>
-__device__ __forceinline__ void march_preview(const DevVdi &v, const ViewConsts &c, Ray &r,
-                                              Accum &acc) {
-    const float hw = 0.5f * (float)v.w, hh = 0.5f * (float)v.h;
-    const int ox = r.ox, oy = r.oy, T = v.T;
-    const float gx0 = r.fx0, gy0 = r.fy0, dgx = r.dgx, dgy = r.dgy;
-    int cx = min(max(ox, 0) / T, v.gw - 1);
-    int cy = min(max(oy, 0) / T, v.gh - 1);
-    const int stx = dgx > 0.f ? 1 : -1, sty = dgy > 0.f ? 1 : -1;
-    const float idgx = rcp_fast(dgx), idgy = rcp_fast(dgy);
-    int bx = (cx + (dgx > 0.f ? 1 : 0)) * T, by = (cy + (dgy > 0.f ? 1 : 0)) * T;  // cell faces, in lists
-    float sx = (dgx != 0.f) ? ((float)(bx - ox) - gx0) * idgx : INFINITY;
-    float sy = (dgy != 0.f) ? ((float)(by - oy) - gy0) * idgy : INFINITY;
-    const float z0 = r.z0, dz = r.dz, idz = rcp_fast(r.dz);
-    const bool inc = dz >= 0.f;
-    int cz = 0;
-    while (cz + 1 < v.nz && z0 >= v.edges[cz + 1]) ++cz;
-    int ez = inc ? cz + 1 : cz;  // index of the next slab edge met
-    float sz = (dz != 0.f) ? (v.edges[ez] - z0) * idz : INFINITY;
-    const float w0 = r.w0, w1 = r.w1, dw = r.dw;
-    int p = -1, plist = -1;  // Algorithm 2's carried index (PW == 0)
-    PairCache pc;
-    pc.k = -1;
-    ColourCache<FMT> cc;
-    cc.k = -1;
-    float s_in = 0.f;
-    const int maxit = v.gw + v.gh + v.nz + 3;
-    for (int it = 0; it < maxit; ++it) {
-        const float s_out = fminf(fminf(fminf(sx, sy), sz), 1.f);
-        if (s_out > s_in) {
-            const uint32_t cnt = __ldg(v.grid + ((size_t)cz * v.gh + cy) * v.gw + cx);
-            if (cnt) {
-                const int fx = min(v.T, v.w - cx * v.T), fy = min(v.T, v.h - cy * v.T);
-                const float ua = s_in * w0 * rcp_fast(fmaf(s_in, dw, w1));
-                const float ub = s_out * w0 * rcp_fast(fmaf(s_out, dw, w1));
-                const float lc = r.lu * (ub - ua);
-                const float want = ((float)cnt / (float)(fx * fy)) * lc * c.cell_scale;
-                // at least one sample per occupied cell; the cap only guards non-finite input
-                const int n = (want < 65536.f) ? max(1, (int)ceilf(want)) : 65536;
-                const float du = (ub - ua) / (float)n, spacing = lc / (float)n;
-                for (int k = 0; k < n; ++k) {
-                    const float uk = fmaf((float)k + 0.5f, du, ua);
-                    const float hx = fmaf(uk, r.h1.x - r.h0.x, r.h0.x);
-                    const float hy = fmaf(uk, r.h1.y - r.h0.y, r.h0.y);
-                    const float hz = fmaf(uk, r.h1.z - r.h0.z, r.h0.z);
-                    const float hwc = fmaf(uk, r.h1.w - r.h0.w, r.h0.w);
-                    const float iw = rcp_fast(hwc);
-                    const float nx = hx * iw, ny = hy * iw, nz = hz * iw;
-                    const int jx = min(max((int)floorf((nx + 1.f) * hw), 0), v.w - 1);
-                    const int jy = min(max((int)floorf((1.f - ny) * hh), 0), v.h - 1);
-                    const int li = jy * v.w + jx;
-                    if (li != plist) {
-                        pc.k = -1;
-                        cc.k = -1;
-                        plist = li;
-                    }
-                    const float2 rg = __ldg(v.range + li);
-                    if (nz < rg.x || nz > rg.y) continue;  // outside every supersegment of the list
-                    int j = v.nsp;
-                    float fj = INFINITY;
-                    if (PW == 0) {
-                        j = first_inc<kSearchAlg2>(v, li, nz, p, pc);
-                        p = min(j, v.nsp - 1);
-                        if (j < v.nsp) {
-                            float b;
-                            get_fb(pc, v, li, j, fj, b);
-                        }
-                    }
-                    const int npairs = v.nsp >> 1;
-                    for (int k0 = 0; PW > 0 && k0 < npairs && j == v.nsp; k0 += (PW > 0 ? PW : 1)) {
-                        float4 d[PW > 0 ? PW : 1];
-#pragma unroll
-                        for (int i = 0; i < PW; ++i)
-                            if (k0 + i < npairs) d[i] = ld_depth_pair(v, k0 + i, li);
-#pragma unroll
-                        for (int i = PW - 1; i >= 0; --i)
-                            if (k0 + i < npairs) {
-                                if (d[i].w >= nz) {
-                                    j = 2 * (k0 + i) + 1;
-                                    fj = d[i].z;
-                                }
-                                if (d[i].y >= nz) {
-                                    j = 2 * (k0 + i);
-                                    fj = d[i].x;
-                                }
-                            }
-                    }
-                    if (j < v.nsp) {
-                        if (fj <= nz) {
-                            add_piece(acc, get_colour<FMT>(cc, v, li, j), spacing);
-                            if (ERT && acc.T <= kErtT) return;
-                        }
-                    }
-                }
-            }
-        }
-        if (s_out >= 1.f) break;
-        if (sx <= sy && sx <= sz) {
-            cx += stx;
-            if ((unsigned)cx >= (unsigned)v.gw) break;
-            bx += stx * T;
-            sx = ((float)(bx - ox) - gx0) * idgx;
-        } else if (sy <= sz) {
-            cy += sty;
-            if ((unsigned)cy >= (unsigned)v.gh) break;
-            by += sty * T;
-            sy = ((float)(by - oy) - gy0) * idgy;
-        } else {
-            cz += inc ? 1 : -1;
-            if ((unsigned)cz >= (unsigned)v.nz) break;
-            ez += inc ? 1 : -1;
-            sz = (v.edges[ez] - z0) * idz;
-        }
-        s_in = fmaxf(s_in, s_out);
-    }
-}
-
 // Pixel of this thread inside a 32 x 8 tile whose warps cover WX x (32/WX)
 // pixels each (lanes on neighbouring pixels walk neighbouring lists).
 template <int WX>

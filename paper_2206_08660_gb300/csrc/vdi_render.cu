@@ -17,15 +17,36 @@
 
 #include "vdi_internal.cuh"
 #include "vdi_march.cuh"
+#include "vdi_preview.cuh"
 
 namespace vdi {
 
 // PATH: 0 = exact walk over every list (the default), 1 = exact walk with
-// empty-space skipping over the count grid, 2 = ray-subsampled preview
-// (D_R > 1), 3 = exact walk with range-block skipping, 4 = ray-subsampled
-// preview with a wide supersegment probe (for launches with few rays), 5 =
-// exact path for a view from V_O's eye (one list per ray).
+// empty-space skipping over the count grid, 3 = exact walk with range-block
+// skipping, 5 = exact path for a view from V_O's eye (one list per ray).  The
+// ray-subsampled previews (D_R > 1) have a kernel of their own below.
 constexpr int kFillTiles = 8;  // tiles outside the box's pixel rectangle per block
+
+// Fill block fb: kFillTiles tiles outside the box's pixel rectangle, whose
+// rays all miss the box: transparent pixels and zero counters.
+__device__ __forceinline__ void fill_tiles(const ViewConsts &c, void *out, int out_fmt, uint32_t *ray_lists,
+                                           uint32_t *ray_segs, int fb) {
+    const int nrect = c.tile_w * c.tile_h;
+    const int ntiles = c.tiles_x * ((c.H + 7) >> 3);
+    const int t0 = nrect + fb * kFillTiles, t1 = min(t0 + kFillTiles, ntiles);
+    const Accum miss = {0.f, 0.f, 0.f, 1.f};
+    for (int t = t0; t < t1; ++t) {
+        int tx, ty;
+        tile_of_block(c, t, tx, ty);
+        const int px = tx * 32 + (threadIdx.x & 31), py = ty * 8 + (threadIdx.x >> 5);
+        if (px < c.W && py < c.H) {
+            const size_t idx = (size_t)py * c.W + px;
+            store_px(out, out_fmt, idx, miss);
+            if (ray_lists) ray_lists[idx] = 0;
+            if (ray_segs) ray_segs[idx] = 0;
+        }
+    }
+}
 
 template <int FMT, int MODE, bool ERT, int WX, int PATH>
 __global__ void __launch_bounds__(256) render_kernel(const ViewConsts c, const DevVdi v, void *out,
@@ -33,22 +54,7 @@ __global__ void __launch_bounds__(256) render_kernel(const ViewConsts c, const D
                                                      uint32_t *ray_segs) {
     const int nrect = c.tile_w * c.tile_h;
     if ((int)blockIdx.x >= nrect) {
-        // kFillTiles tiles outside the box's pixel rectangle: every ray misses
-        // the box, so the pixels are transparent and the counters zero
-        const int ntiles = c.tiles_x * ((c.H + 7) >> 3);
-        const int t0 = nrect + ((int)blockIdx.x - nrect) * kFillTiles, t1 = min(t0 + kFillTiles, ntiles);
-        const Accum miss = {0.f, 0.f, 0.f, 1.f};
-        for (int t = t0; t < t1; ++t) {
-            int tx, ty;
-            tile_of_block(c, t, tx, ty);
-            const int px = tx * 32 + (threadIdx.x & 31), py = ty * 8 + (threadIdx.x >> 5);
-            if (px < c.W && py < c.H) {
-                const size_t idx = (size_t)py * c.W + px;
-                store_px(out, out_fmt, idx, miss);
-                if (ray_lists) ray_lists[idx] = 0;
-                if (ray_segs) ray_segs[idx] = 0;
-            }
-        }
+        fill_tiles(c, out, out_fmt, ray_lists, ray_segs, (int)blockIdx.x - nrect);
         return;
     }
     int lx, ly, tx, ty;
@@ -60,11 +66,7 @@ __global__ void __launch_bounds__(256) render_kernel(const ViewConsts c, const D
     uint32_t nl = 0, nsg = 0;
     Ray r;
     if (setup_ray(c, px, py, v.w, v.h, r)) {
-        if (PATH == 2)
-            march_preview<FMT, ERT, 3>(v, c, r, acc);
-        else if (PATH == 4)
-            march_preview<FMT, ERT, 10>(v, c, r, acc);
-        else if (PATH == 1)
+        if (PATH == 1)
             march_exact_ess<FMT, MODE, ERT>(v, r, acc, nl, nsg);
         else if (PATH == 3)
             march_exact<FMT, MODE, ERT, false, true>(v, r, acc, nl, nsg);
@@ -79,6 +81,46 @@ __global__ void __launch_bounds__(256) render_kernel(const ViewConsts c, const D
     store_px(out, out_fmt, idx, acc);
     if (ray_lists) ray_lists[idx] = nl;
     if (ray_segs) ray_segs[idx] = nsg;
+}
+
+// Ray-subsampled preview (Section 4.4) with L lanes per ray: the blocks of a
+// 32 x 8 tile meeting the box's pixel rectangle (L blocks per tile, 256 / L
+// rays each) come first, then the fill blocks of the tiles outside it.
+template <int FMT, int L>
+__global__ void __launch_bounds__(256, 4) preview_kernel(const ViewConsts c, const DevVdi v, void *out, int out_fmt) {
+    constexpr int ROWS = 8 / L;  // tile rows per block
+    const int nrect = c.tile_w * c.tile_h;
+    if ((int)blockIdx.x >= nrect * L) {
+        fill_tiles(c, out, out_fmt, nullptr, nullptr, (int)blockIdx.x - nrect * L);
+        return;
+    }
+    const int tile = (int)blockIdx.x / L, unit = (int)blockIdx.x - tile * L;
+    int tx, ty;
+    tile_of_block(c, tile, tx, ty);
+    const int g = (int)threadIdx.x / L;  // this lane's ray within the block
+    const int px = tx * 32 + (g & 31), py = ty * 8 + unit * ROWS + (g >> 5);
+    const bool inside = px < c.W && py < c.H;
+    Ray r = {};
+    const bool active = inside && setup_ray(c, px, py, v.w, v.h, r);
+    const Accum acc = march_preview_lanes<FMT, kPreviewProbe, L>(v, c, r, active);
+    if (inside && (threadIdx.x & (L - 1)) == 0) store_px(out, out_fmt, (size_t)py * c.W + px, acc);
+}
+
+template <int FMT, int L>
+static cudaError_t launch_preview_l(const ViewConsts &c, const DevVdi &v, void *out, int out_fmt, cudaStream_t st) {
+    const int nrect = c.tile_w * c.tile_h, ntiles = div_up(c.W, 32) * div_up(c.H, 8);
+    preview_kernel<FMT, L><<<nrect * L + div_up(ntiles - nrect, kFillTiles), 256, 0, st>>>(c, v, out, out_fmt);
+    return cudaGetLastError();
+}
+
+// lanes per preview ray: more for launches with few rays, whose time is the
+// longest ray's chain of dependent loads (the image is the same for any count)
+template <int FMT>
+static cudaError_t launch_preview(const ViewConsts &c, const DevVdi &v, void *out, int out_fmt, cudaStream_t st) {
+    const long long rays = (long long)c.W * c.H;
+    if (rays <= 300000) return launch_preview_l<FMT, 8>(c, v, out, out_fmt, st);
+    if (rays <= 1200000) return launch_preview_l<FMT, 4>(c, v, out, out_fmt, st);
+    return launch_preview_l<FMT, 2>(c, v, out, out_fmt, st);
 }
 
 // Instrumented exact render: marks the VDI words the algorithm reads.
@@ -184,6 +226,12 @@ cudaError_t launch_count_totals(const uint32_t *lists, const uint32_t *segs, lon
 // launchers
 // ---------------------------------------------------------------------------
 
+#define CK_RET(call)                      \
+    do {                                  \
+        cudaError_t e_ = (call);          \
+        if (e_ != cudaSuccess) return e_; \
+    } while (0)
+
 template <int FMT, int MODE, bool ERT, int PATH>
 static cudaError_t launch_ws(const ViewConsts &c, const DevVdi &v, void *out, int out_fmt, uint32_t *rl,
                              uint32_t *rs, int warp_shape, cudaStream_t st) {
@@ -207,11 +255,11 @@ template <int FMT, int MODE>
 static cudaError_t launch_m(const ViewConsts &c, const DevVdi &v, void *out, int out_fmt, uint32_t *rl,
                             uint32_t *rs, int warp_shape, bool ert, bool ess, bool blocks, cudaStream_t st) {
     if (c.d_r > 1) {
-        // previews ignore the search mode (their samples use a wide probe); a
-        // launch of up to about two waves of rays takes the widest probe
-        if ((long long)c.W * c.H <= 300000)
-            return launch_ws<FMT, kSearchAlg2, true, 4>(c, v, out, out_fmt, rl, rs, warp_shape, st);
-        return launch_ws<FMT, kSearchAlg2, true, 2>(c, v, out, out_fmt, rl, rs, warp_shape, st);
+        // previews ignore the search mode and the warp shape (their samples use
+        // a wide probe, several lanes serve a ray); their counters stay zero
+        if (rl) CK_RET(cudaMemsetAsync(rl, 0, sizeof(uint32_t) * c.W * c.H, st));
+        if (rs) CK_RET(cudaMemsetAsync(rs, 0, sizeof(uint32_t) * c.W * c.H, st));
+        return launch_preview<FMT>(c, v, out, out_fmt, st);
     }
     // per-ray counters count whole lists, so they come from the walk over every list
     if (!ert) return launch_ws<FMT, MODE, false, 0>(c, v, out, out_fmt, rl, rs, warp_shape, st);

@@ -95,7 +95,7 @@ def test_stats_frame_totals(V, ctx, orc, no_ert):
             if no_ert:
                 assert np.array_equal(gs[ok], nsg[ok])
             else:
-                assert np.all(gs[ok] <= nsg[ok]) and st.pieces < nsg.sum()  # early termination ends rays
+                assert np.all(gs[ok] <= nsg[ok]) and st.pieces <= nsg.sum()  # early termination can end rays
             assert st.rays_hit > 100
         with pytest.raises(V.VdiError):  # previews are not counted
             V.vdi_render_ex(vdi, cam, W, H, 1, 2, out, record_stats=True)
