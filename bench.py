@@ -83,7 +83,7 @@ def peaks():
 
 def render_kernel_hash() -> str:
     h = hashlib.sha1()
-    for fn in ("vdi_render.cu", "vdi_march.cuh", "vdi_internal.cuh"):
+    for fn in ("vdi_render.cu", "vdi_march.cuh", "vdi_internal.cuh", "vdi_preview.cuh"):
         with open(os.path.join(ROOT, "paper_2206_08660_gb300", "csrc", fn), "rb") as f:
             h.update(f.read())
     return h.hexdigest()[:12]
@@ -102,6 +102,38 @@ def recorded_traffic(workload: str):
             if len(parts) >= 4 and parts[2] == "kernel_hash" and parts[3] == want:
                 return int(parts[1])
     return None
+
+
+def recorded_instructions(workload: str):
+    """Warp instructions per exact-render launch of each step frame (ncu
+    smsp__inst_executed.sum) from the committed summary, if it was taken on the
+    current kernel source; else None.  Line format:
+    warp_instructions_per_launch: <deg>=<count> ... kernel_hash <hash>"""
+    p = os.path.join(ROOT, "profiles", f"render_exact_{workload}.md")
+    if not os.path.exists(p):
+        return None
+    want = render_kernel_hash()
+    for line in open(p):
+        if line.startswith("warp_instructions_per_launch:"):
+            parts = line.split()
+            if len(parts) >= 4 and parts[-2] == "kernel_hash" and parts[-1] == want:
+                return {k: int(v) for k, v in (x.split("=") for x in parts[1:-2])}
+    return None
+
+
+def issue_peak():
+    """Warp instructions per second the GPU can issue: 4 schedulers per SM, one
+    instruction per scheduler and cycle, at the maximum SM clock."""
+    import torch
+
+    sms = torch.cuda.get_device_properties(torch.cuda.current_device()).multi_processor_count
+    mhz = 2070.0
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            mhz = float(json.load(f).get("sm_max_mhz", mhz))
+    except Exception:
+        pass
+    return sms * 4 * mhz * 1e6, sms, mhz
 
 
 class ClockSampler:
@@ -697,6 +729,19 @@ def main():
     achieved = float(np.sum(touched) / (np.sum(exact_ms) / 1e3) / 1e9) if exact else 0.0
     peak, peak_src = peaks()
     traffic = recorded_traffic(args.workload)
+    # the same kernel against the instruction-issue roofline: it re-reads each
+    # unique byte from L1/L2 for about twenty rays and is bound by issue, not HBM
+    instr = recorded_instructions(args.workload)
+    roofline_issue = None
+    if exact and instr and all(f"{wl['frames'][i][0]:g}deg" in instr for i in exact):
+        ipeak, sms, mhz = issue_peak()
+        inst = float(sum(instr[f"{wl['frames'][i][0]:g}deg"] for i in exact))
+        ia = inst / (np.sum(exact_ms) / 1e3)
+        roofline_issue = {"bound": "issue", "achieved": ia, "peak": ipeak, "unit": "warp instructions/s",
+                          "frac": ia / ipeak, "instructions_per_step": inst,
+                          "peak_derivation": f"{sms} SMs x 4 schedulers x 1 instruction/cycle x {mhz:g} MHz",
+                          "source": "ncu smsp__inst_executed.sum per launch (profiles/render_exact_"
+                                    f"{args.workload}.md) / event-timed duration"}
 
     # ---- the same kernel near the original view (0 and 5 degrees), where a frame
     # streams most of the VDI rather than walking many lists
@@ -837,6 +882,7 @@ def main():
                      "algorithmic_bytes_per_launch": [int(b) for b in touched],
                      "frac_per_frame": {f"{wl['frames'][i][0]:g}deg": float(tb / (ms / 1e3) / 1e9 / peak)
                                         for i, tb, ms in zip(exact, touched, exact_ms)}},
+        "roofline_issue": roofline_issue,
         "clocks": clocks, "e2e": e2e, "gpu_launches": launches_per_step * args.steps, "ablation": ablation,
         "roofline_near_original_view": near, "batched_step": batched_step, "batched_workload": batched_config,
         "vdi_generate_ms": gen_s * 1e3, "generation": generation, "quality": quality, "preview_control": control, "vdi_bytes": int(layout.depth_bytes + layout.colour_bytes),

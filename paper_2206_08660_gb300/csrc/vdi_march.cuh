@@ -416,7 +416,7 @@ __device__ __forceinline__ void march_exact(const DevVdi &v, Ray &r, Accum &acc,
 // process_list's, so the image is the same.  Any other ray takes the list
 // walk.
 // ---------------------------------------------------------------------------
-constexpr int kSinglePF = 4;  // slot pairs march_single requests at once
+constexpr int kSinglePF = 2;  // slot pairs march_single requests at once
 
 template <int FMT, int MODE, bool ERT>
 __device__ __forceinline__ void march_single(const DevVdi &v, Ray &r, Accum &acc, uint32_t &n_lists,

@@ -48,8 +48,11 @@ __device__ __forceinline__ void fill_tiles(const ViewConsts &c, void *out, int o
     }
 }
 
+// The one-list path for views from V_O's eye (PATH 5) waits on its records
+// rather than on arithmetic: it runs with six blocks per SM (register cap)
+// and requests slot pairs two at a time.
 template <int FMT, int MODE, bool ERT, int WX, int PATH>
-__global__ void __launch_bounds__(256) render_kernel(const ViewConsts c, const DevVdi v, void *out,
+__global__ void __launch_bounds__(256, PATH == 5 ? 6 : 1) render_kernel(const ViewConsts c, const DevVdi v, void *out,
                                                      int out_fmt, uint32_t *ray_lists,
                                                      uint32_t *ray_segs) {
     const int nrect = c.tile_w * c.tile_h;
