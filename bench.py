@@ -370,9 +370,12 @@ def serving_leg(V, torch, ctx, dev, cfg=SERVING):
             while time.monotonic() - t_start < arrivals[-1]:
                 time.sleep(cfg["replace_every"])
                 slot = k % cfg["n_vdis"]
+                # generation through the server: the new VDI's bytes are charged to
+                # the device budget before it is allocated on the side stream
+                c = S.orbit_camera(bmin, bmax, cfg["w"] / cfg["h"], az_deg=az0[slot] + 5.0 * (k + 1), el_deg=20.0)
                 with torch.cuda.stream(side):
-                    vdi, _ = gen(slot, V.VDI_F16, az=az0[slot] + 5.0 * (k + 1), stream=side)
-                V.vdi_server_set_vdi(srv, slot, vdi, side)
+                    V.vdi_server_generate(srv, slot, vol_d, bmin, bmax, kn, V.camera(c.view, c.proj), cfg["w"],
+                                          cfg["h"], cfg["ns"], cfg["tau"], u, u, V.VDI_F16, stream=side)
                 k += 1
 
         ts, tr = th.Thread(target=submitter), th.Thread(target=replacer)
@@ -395,7 +398,8 @@ def serving_leg(V, torch, ctx, dev, cfg=SERVING):
         open_loop = {"offered_rps": cfg["rate"], "requests": n, "failed": fails,
                      "p50_ms": float(np.percentile(lat, 50)), "p99_ms": float(np.percentile(lat, 99)),
                      "throughput_rps": len(lat) / wall, "mean_batch": st.batched_requests / max(st.batches, 1),
-                     "vdi_replacements": int(st.vdi_installs) - cfg["n_vdis"]}
+                     "vdi_replacements": int(st.vdi_installs) - cfg["n_vdis"],
+                     "resident_vdi_bytes_at_end": int(st.vdi_bytes), "budget_bytes": cfg["budget"]}
 
         # ---- saturated throughput, same request mix: batched server (FP16) ...
         sat = make_requests(512)

@@ -41,9 +41,15 @@ struct BatchReq {
     int tile_base;   // first tile of this request in the queue
 };
 
+// Two tile queues: exact requests (32 x 8 tiles, one lane per ray) and
+// ray-subsampled previews (32 x (8 / kBatchLanes) tiles, kBatchLanes lanes per
+// ray), each pulled by its own persistent kernel from its own counter.  A
+// request's tile_base counts within its queue; ex_idx / pv_idx list the
+// requests of each queue in queue order.
 struct BatchParams {
-    int n_req, total_tiles;
-    unsigned *counter;
+    int n_req, total_tiles, total_ptiles, n_ex, n_pv;
+    unsigned *counter, *pcounter;
+    unsigned char ex_idx[kMaxBatchReq], pv_idx[kMaxBatchReq];
     DevVdi vdis[kMaxBatchVdi];
     BatchReq reqs[kMaxBatchReq];
 };
@@ -62,69 +68,85 @@ struct UpParams {
     UpReq reqs[kMaxBatchReq];
 };
 
-// PREVIEW: the batch holds ray-subsampled previews (d_r > 1); without them the
-// kernel carries only the exact walk, which needs fewer registers, so more
-// blocks fit on an SM.
-template <int WX, bool PREVIEW>
-__global__ void __launch_bounds__(256, PREVIEW ? 3 : 4) batch_render_kernel(const BatchParams P) {
+// The request of queue tile t: the last request in idx (queue order) whose
+// tile_base is at most t.
+__device__ __forceinline__ int queue_request(const BatchParams &P, const unsigned char *idx, int n, int t) {
+    int lo = 0, hi = n - 1;
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (P.reqs[idx[mid]].tile_base <= t)
+            lo = mid;
+        else
+            hi = mid - 1;
+    }
+    return idx[lo];
+}
+
+// The next tile of a queue for the whole block (thread 0 takes it from the
+// counter); returns the tile (>= total when the queue is drained) and its request.
+__device__ __forceinline__ int next_tile(const BatchParams &P, unsigned *counter, const unsigned char *idx, int n,
+                                         int total, int &req) {
     __shared__ int s_tile, s_req;
+    if (threadIdx.x == 0) {
+        const int t = (int)atomicAdd(counter, 1u);
+        s_tile = t;
+        s_req = (t < total) ? queue_request(P, idx, n, t) : 0;
+    }
+    __syncthreads();
+    const int t = s_tile;
+    req = s_req;
+    __syncthreads();  // every thread has read s_tile / s_req before thread 0 writes them again
+    return t;
+}
+
+// Exact requests: the list walk of vdi_render, one lane per ray.
+template <int WX>
+__global__ void __launch_bounds__(256, 4) batch_render_kernel(const BatchParams P) {
     for (;;) {
-        if (threadIdx.x == 0) {
-            const int t = (int)atomicAdd(P.counter, 1u);
-            int r = 0;
-            if (t < P.total_tiles) {
-                int lo = 0, hi = P.n_req - 1;  // last request with tile_base <= t
-                while (lo < hi) {
-                    const int mid = (lo + hi + 1) >> 1;
-                    if (P.reqs[mid].tile_base <= t)
-                        lo = mid;
-                    else
-                        hi = mid - 1;
-                }
-                r = lo;
-            }
-            s_tile = t;
-            s_req = r;
-        }
-        __syncthreads();
-        const int tile = s_tile, r = s_req;
-        if (tile >= P.total_tiles) return;  // uniform: every thread read the same s_tile
+        int r;
+        const int tile = next_tile(P, P.counter, P.ex_idx, P.n_ex, P.total_tiles, r);
+        if (tile >= P.total_tiles) return;  // uniform: every thread read the same tile
         const BatchReq &q = P.reqs[r];
         const DevVdi &v = P.vdis[q.vdi];
         const int local = tile - q.tile_base;
         const int tx0 = (local % q.tiles_x) * 32, ty0 = (local / q.tiles_x) * 8;
-        if (PREVIEW && q.c.d_r > 1) {
-            // a preview tile in kBatchLanes passes of 256 / kBatchLanes rays with
-            // kBatchLanes lanes per ray (the same image as any lane count)
-            const int g = (int)threadIdx.x / kBatchLanes;
-            for (int unit = 0; unit < kBatchLanes; ++unit) {
-                const int px = tx0 + (g & 31), py = ty0 + unit * (8 / kBatchLanes) + (g >> 5);
-                const bool inside = px < q.c.W && py < q.c.H;
-                Ray ray = {};
-                const bool active = inside && setup_ray(q.c, px, py, v.w, v.h, ray);
-                const Accum acc = (v.fmt == 0) ? march_preview_lanes<0, kPreviewProbe, kBatchLanes>(v, q.c, ray, active)
-                                               : march_preview_lanes<1, kPreviewProbe, kBatchLanes>(v, q.c, ray, active);
-                if (inside && (threadIdx.x & (kBatchLanes - 1)) == 0)
-                    store_px(q.out, q.out_fmt, (size_t)py * q.c.W + px, acc);
+        int lx, ly;
+        tile_offset<WX>(lx, ly);
+        const int px = tx0 + lx, py = ty0 + ly;
+        if (px < q.c.W && py < q.c.H) {
+            Accum acc = {0.f, 0.f, 0.f, 1.f};
+            uint32_t nl = 0, nsg = 0;
+            Ray ray;
+            if (setup_ray(q.c, px, py, v.w, v.h, ray)) {
+                if (v.fmt == 0)
+                    march_exact<0, kSearchAlg2, true>(v, ray, acc, nl, nsg);
+                else
+                    march_exact<1, kSearchAlg2, true>(v, ray, acc, nl, nsg);
             }
-        } else {
-            int lx, ly;
-            tile_offset<WX>(lx, ly);
-            const int px = tx0 + lx, py = ty0 + ly;
-            if (px < q.c.W && py < q.c.H) {
-                Accum acc = {0.f, 0.f, 0.f, 1.f};
-                uint32_t nl = 0, nsg = 0;
-                Ray ray;
-                if (setup_ray(q.c, px, py, v.w, v.h, ray)) {
-                    if (v.fmt == 0)
-                        march_exact<0, kSearchAlg2, true>(v, ray, acc, nl, nsg);
-                    else
-                        march_exact<1, kSearchAlg2, true>(v, ray, acc, nl, nsg);
-                }
-                store_px(q.out, q.out_fmt, (size_t)py * q.c.W + px, acc);
-            }
+            store_px(q.out, q.out_fmt, (size_t)py * q.c.W + px, acc);
         }
-        __syncthreads();  // every thread has read s_tile / s_req before thread 0 writes them again
+    }
+}
+
+// Ray-subsampled previews: kBatchLanes lanes per ray (the same image as the
+// single-view kernels' lane counts).
+__global__ void __launch_bounds__(256, 3) batch_preview_kernel(const BatchParams P) {
+    constexpr int rows = 8 / kBatchLanes;
+    const int g = (int)threadIdx.x / kBatchLanes;
+    for (;;) {
+        int r;
+        const int tile = next_tile(P, P.pcounter, P.pv_idx, P.n_pv, P.total_ptiles, r);
+        if (tile >= P.total_ptiles) return;
+        const BatchReq &q = P.reqs[r];
+        const DevVdi &v = P.vdis[q.vdi];
+        const int local = tile - q.tile_base;
+        const int px = (local % q.tiles_x) * 32 + (g & 31), py = (local / q.tiles_x) * rows + (g >> 5);
+        const bool inside = px < q.c.W && py < q.c.H;
+        Ray ray = {};
+        const bool active = inside && setup_ray<false>(q.c, px, py, v.w, v.h, ray);
+        const Accum acc = (v.fmt == 0) ? march_preview_lanes<0, kPreviewProbe, kBatchLanes>(v, q.c, ray, active)
+                                       : march_preview_lanes<1, kPreviewProbe, kBatchLanes>(v, q.c, ray, active);
+        if (inside && (threadIdx.x & (kBatchLanes - 1)) == 0) store_px(q.out, q.out_fmt, (size_t)py * q.c.W + px, acc);
     }
 }
 
@@ -163,16 +185,11 @@ __global__ void __launch_bounds__(256) batch_upsample_kernel(const UpParams P) {
     store_px(q.out, q.out_fmt, (size_t)Y * q.W + X, acc);
 }
 
-template <bool PREVIEW>
-static const void *render_fn_p(int ws) {
-    if (ws == 0) return (const void *)batch_render_kernel<32, PREVIEW>;
-    if (ws == 1) return (const void *)batch_render_kernel<16, PREVIEW>;
-    if (ws == 2) return (const void *)batch_render_kernel<8, PREVIEW>;
-    return (const void *)batch_render_kernel<4, PREVIEW>;
-}
-
-static const void *render_fn(int ws, bool preview) {
-    return preview ? render_fn_p<true>(ws) : render_fn_p<false>(ws);
+static const void *render_fn(int ws) {
+    if (ws == 0) return (const void *)batch_render_kernel<32>;
+    if (ws == 1) return (const void *)batch_render_kernel<16>;
+    if (ws == 2) return (const void *)batch_render_kernel<8>;
+    return (const void *)batch_render_kernel<4>;
 }
 
 // ---------------------------------------------------------------------------
@@ -199,8 +216,8 @@ static vdi_status plan_batch(vdi_ctx *ctx, const vdi_request *reqs, int n, Batch
     memset(pl.bp, 0, sizeof(BatchParams));
     memset(pl.up, 0, sizeof(UpParams));
     std::vector<const vdi_t *> vdis;
-    size_t off = 256;  // the counter lives at offset 0
-    int tiles = 0, up_tiles = 0;
+    size_t off = 256;  // the two queue counters live at offsets 0 and 4
+    int tiles = 0, ptiles = 0, up_tiles = 0;
     pl.lo_offset.assign(n, (size_t)-1);
     pl.final_out.assign(n, nullptr);
     for (int i = 0; i < n; ++i) {
@@ -213,7 +230,7 @@ static vdi_status plan_batch(vdi_ctx *ctx, const vdi_request *reqs, int n, Batch
         if ((r.Wr != 0 || r.Hr != 0) && (r.Wr < 1 || r.Hr < 1 || r.Wr > r.W || r.Hr > r.H))
             return fail(VDI_ERR_INVALID_ARG, "request %d: rays %dx%d for image %dx%d", i, r.Wr, r.Hr, r.W, r.H);
         if (r.vdi->ctx != ctx) return fail(VDI_ERR_INVALID_ARG, "request %d: VDI of another context", i);
-        if (r.d_r > 1) pl.preview = true;
+
         int vi = -1;
         for (size_t k = 0; k < vdis.size(); ++k)
             if (vdis[k] == r.vdi) vi = (int)k;
@@ -234,8 +251,16 @@ static vdi_status plan_batch(vdi_ctx *ctx, const vdi_request *reqs, int n, Batch
         }
         q.vdi = vi;
         q.tiles_x = div_up(Wr, 32);
-        q.tile_base = tiles;
-        tiles += q.tiles_x * div_up(Hr, 8);
+        if (r.d_r > 1) {  // preview queue: 32 x (8 / kBatchLanes) tiles
+            pl.preview = true;
+            q.tile_base = ptiles;
+            ptiles += q.tiles_x * div_up(Hr, 8 / kBatchLanes);
+            pl.bp->pv_idx[pl.bp->n_pv++] = (unsigned char)i;
+        } else {  // exact queue: 32 x 8 tiles
+            q.tile_base = tiles;
+            tiles += q.tiles_x * div_up(Hr, 8);
+            pl.bp->ex_idx[pl.bp->n_ex++] = (unsigned char)i;
+        }
         pl.final_out[i] = r.out;
         if (Wr == r.W && Hr == r.H) {
             q.out = r.out;
@@ -258,6 +283,7 @@ static vdi_status plan_batch(vdi_ctx *ctx, const vdi_request *reqs, int n, Batch
     }
     pl.bp->n_req = n;
     pl.bp->total_tiles = tiles;
+    pl.bp->total_ptiles = ptiles;
     pl.up->total_tiles = up_tiles;
     pl.scratch_bytes = off;
     return VDI_OK;
@@ -266,6 +292,7 @@ static vdi_status plan_batch(vdi_ctx *ctx, const vdi_request *reqs, int n, Batch
 // point the plan at a scratch allocation
 static void bind_scratch(BatchPlan &pl, char *scratch) {
     pl.bp->counter = reinterpret_cast<unsigned *>(scratch);
+    pl.bp->pcounter = reinterpret_cast<unsigned *>(scratch) + 1;
     int k = 0;
     for (int i = 0; i < pl.bp->n_req; ++i)
         if (pl.lo_offset[i] != (size_t)-1) {
@@ -274,19 +301,29 @@ static void bind_scratch(BatchPlan &pl, char *scratch) {
         }
 }
 
-static int persistent_blocks(vdi_ctx *ctx, int ws, int bps, bool preview) {
+// persistent grid of the exact kernel: resident blocks per SM (capped at bps
+// when bps > 0) times the SM count, no more blocks than tiles
+static int exact_grid(vdi_ctx *ctx, const BatchPlan &pl, int ws, int bps) {
     int occ = 1;
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, render_fn(ws, preview), 256, 0);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, render_fn(ws), 256, 0);
     if (bps > 0) occ = std::min(occ, bps);
-    return std::max(1, occ) * ctx->sm_count;
+    return std::min(std::max(1, occ) * ctx->sm_count, std::max(1, pl.bp->total_tiles));
+}
+
+static int preview_grid(vdi_ctx *ctx, const BatchPlan &pl) {
+    int occ = 1;
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, (const void *)batch_preview_kernel, 256, 0);
+    return std::min(std::max(1, occ) * ctx->sm_count, std::max(1, pl.bp->total_ptiles));
 }
 
 static cudaError_t enqueue_plain(vdi_ctx *ctx, BatchPlan &pl, int ws, int bps, cudaStream_t st) {
-    cudaError_t e = cudaMemsetAsync(pl.bp->counter, 0, sizeof(unsigned), st);
+    cudaError_t e = cudaMemsetAsync(pl.bp->counter, 0, 2 * sizeof(unsigned), st);
     if (e != cudaSuccess) return e;
-    const int grid = std::min(persistent_blocks(ctx, ws, bps, pl.preview), std::max(1, pl.bp->total_tiles));
     void *args[] = {pl.bp};
-    e = cudaLaunchKernel(render_fn(ws, pl.preview), dim3(grid), dim3(256), args, 0, st);
+    if (pl.bp->n_ex) e = cudaLaunchKernel(render_fn(ws), dim3(exact_grid(ctx, pl, ws, bps)), dim3(256), args, 0, st);
+    if (e != cudaSuccess) return e;
+    if (pl.bp->n_pv)
+        e = cudaLaunchKernel((const void *)batch_preview_kernel, dim3(preview_grid(ctx, pl)), dim3(256), args, 0, st);
     if (e != cudaSuccess || pl.up->n == 0) return e;
     void *uargs[] = {pl.up};
     return cudaLaunchKernel((const void *)batch_upsample_kernel, dim3(pl.up->total_tiles), dim3(256), uargs, 0, st);
@@ -297,9 +334,9 @@ static cudaError_t enqueue_plain(vdi_ctx *ctx, BatchPlan &pl, int ws, int bps, c
 struct GraphEntry {
     cudaGraph_t graph = nullptr;
     cudaGraphExec_t exec = nullptr;
-    cudaGraphNode_t render_node = nullptr, up_node = nullptr;
+    cudaGraphNode_t render_node = nullptr, preview_node = nullptr, up_node = nullptr;
     void *scratch = nullptr;
-    int grid = 0;
+    int grid = 0, pgrid = 0;
 };
 
 struct BatchCache {
@@ -345,6 +382,17 @@ static std::string tune_key(const vdi_request *reqs, int n) {
     return k;
 }
 
+static cudaKernelNodeParams kernel_node(const void *fn, int grid, void **args) {
+    cudaKernelNodeParams kp{};
+    kp.func = const_cast<void *>(fn);
+    kp.gridDim = dim3(grid);
+    kp.blockDim = dim3(256);
+    kp.kernelParams = args;
+    return kp;
+}
+
+// memset(counters) -> {persistent exact kernel, persistent preview kernel} ->
+// batched upsample; a replay of the same shape only updates kernel parameters
 static vdi_status enqueue_graph(vdi_ctx *ctx, const vdi_request *reqs, int n, BatchPlan &pl, int ws, int bps,
                                 cudaStream_t st) {
     BatchCache &bc = cache_of(ctx);
@@ -352,71 +400,62 @@ static vdi_status enqueue_graph(vdi_ctx *ctx, const vdi_request *reqs, int n, Ba
     const std::string key = shape_key(reqs, n, pl, ws, bps, st);
     auto it = bc.graphs.find(key);
     cudaError_t e = cudaSuccess;
+    void *args[] = {pl.bp};
+    void *uargs[] = {pl.up};
     if (it == bc.graphs.end()) {
         GraphEntry ge;
         if ((e = cudaMalloc(&ge.scratch, pl.scratch_bytes)) != cudaSuccess) return cuda_fail(e, "graph scratch");
         bind_scratch(pl, (char *)ge.scratch);
-        ge.grid = std::min(persistent_blocks(ctx, ws, bps, pl.preview), std::max(1, pl.bp->total_tiles));
+        ge.grid = exact_grid(ctx, pl, ws, bps);
+        ge.pgrid = preview_grid(ctx, pl);
         cudaGraphNode_t ms = nullptr;
         cudaMemsetParams mp{};
         mp.dst = ge.scratch;
         mp.value = 0;
         mp.elementSize = 4;
-        mp.width = 1;
+        mp.width = 2;
         mp.height = 1;
-        mp.pitch = 4;
-        void *args[] = {pl.bp};
-        cudaKernelNodeParams kp{};
-        kp.func = (void *)render_fn(ws, pl.preview);
-        kp.gridDim = dim3(ge.grid);
-        kp.blockDim = dim3(256);
-        kp.kernelParams = args;
-        if ((e = cudaGraphCreate(&ge.graph, 0)) != cudaSuccess ||
-            (e = cudaGraphAddMemsetNode(&ms, ge.graph, nullptr, 0, &mp)) != cudaSuccess ||
-            (e = cudaGraphAddKernelNode(&ge.render_node, ge.graph, &ms, 1, &kp)) != cudaSuccess) {
+        mp.pitch = 8;
+        std::vector<cudaGraphNode_t> renders;
+        e = cudaGraphCreate(&ge.graph, 0);
+        if (e == cudaSuccess) e = cudaGraphAddMemsetNode(&ms, ge.graph, nullptr, 0, &mp);
+        if (e == cudaSuccess && pl.bp->n_ex) {
+            const cudaKernelNodeParams kp = kernel_node(render_fn(ws), ge.grid, args);
+            e = cudaGraphAddKernelNode(&ge.render_node, ge.graph, &ms, 1, &kp);
+            renders.push_back(ge.render_node);
+        }
+        if (e == cudaSuccess && pl.bp->n_pv) {
+            const cudaKernelNodeParams kp = kernel_node((const void *)batch_preview_kernel, ge.pgrid, args);
+            e = cudaGraphAddKernelNode(&ge.preview_node, ge.graph, &ms, 1, &kp);
+            renders.push_back(ge.preview_node);
+        }
+        if (e == cudaSuccess && pl.up->n) {
+            const cudaKernelNodeParams kp = kernel_node((const void *)batch_upsample_kernel, pl.up->total_tiles, uargs);
+            e = cudaGraphAddKernelNode(&ge.up_node, ge.graph, renders.data(), renders.size(), &kp);
+        }
+        if (e == cudaSuccess) e = cudaGraphInstantiate(&ge.exec, ge.graph, 0);
+        if (e != cudaSuccess) {
+            if (ge.graph) cudaGraphDestroy(ge.graph);
             cudaFree(ge.scratch);
             return cuda_fail(e, "graph build");
-        }
-        if (pl.up->n) {
-            void *uargs[] = {pl.up};
-            cudaKernelNodeParams up{};
-            up.func = (void *)batch_upsample_kernel;
-            up.gridDim = dim3(pl.up->total_tiles);
-            up.blockDim = dim3(256);
-            up.kernelParams = uargs;
-            if ((e = cudaGraphAddKernelNode(&ge.up_node, ge.graph, &ge.render_node, 1, &up)) != cudaSuccess) {
-                cudaGraphDestroy(ge.graph);
-                cudaFree(ge.scratch);
-                return cuda_fail(e, "graph build");
-            }
-        }
-        if ((e = cudaGraphInstantiate(&ge.exec, ge.graph, 0)) != cudaSuccess) {
-            cudaGraphDestroy(ge.graph);
-            cudaFree(ge.scratch);
-            return cuda_fail(e, "graph instantiate");
         }
         it = bc.graphs.emplace(key, ge).first;
     } else {
         GraphEntry &ge = it->second;
         bind_scratch(pl, (char *)ge.scratch);
-        void *args[] = {pl.bp};
-        cudaKernelNodeParams kp{};
-        kp.func = (void *)render_fn(ws, pl.preview);
-        kp.gridDim = dim3(ge.grid);
-        kp.blockDim = dim3(256);
-        kp.kernelParams = args;
-        if ((e = cudaGraphExecKernelNodeSetParams(ge.exec, ge.render_node, &kp)) != cudaSuccess)
-            return cuda_fail(e, "graph update");
-        if (pl.up->n) {
-            void *uargs[] = {pl.up};
-            cudaKernelNodeParams up{};
-            up.func = (void *)batch_upsample_kernel;
-            up.gridDim = dim3(pl.up->total_tiles);
-            up.blockDim = dim3(256);
-            up.kernelParams = uargs;
-            if ((e = cudaGraphExecKernelNodeSetParams(ge.exec, ge.up_node, &up)) != cudaSuccess)
-                return cuda_fail(e, "graph update");
+        if (ge.render_node) {
+            const cudaKernelNodeParams kp = kernel_node(render_fn(ws), ge.grid, args);
+            e = cudaGraphExecKernelNodeSetParams(ge.exec, ge.render_node, &kp);
         }
+        if (e == cudaSuccess && ge.preview_node) {
+            const cudaKernelNodeParams kp = kernel_node((const void *)batch_preview_kernel, ge.pgrid, args);
+            e = cudaGraphExecKernelNodeSetParams(ge.exec, ge.preview_node, &kp);
+        }
+        if (e == cudaSuccess && ge.up_node) {
+            const cudaKernelNodeParams kp = kernel_node((const void *)batch_upsample_kernel, pl.up->total_tiles, uargs);
+            e = cudaGraphExecKernelNodeSetParams(ge.exec, ge.up_node, &kp);
+        }
+        if (e != cudaSuccess) return cuda_fail(e, "graph update");
     }
     if ((e = cudaGraphLaunch(it->second.exec, st)) != cudaSuccess) return cuda_fail(e, "graph launch");
     return VDI_OK;
@@ -488,12 +527,10 @@ VDI_API vdi_status vdi_autotune_batch(vdi_ctx *ctx, const vdi_request *reqs, int
     cudaEventCreate(&e1);
     vdi_batch_opts winner = {0, 0, 0};
     float wms = INFINITY;
-    bool preview = false;
-    for (int i = 0; i < n; ++i) preview = preview || reqs[i].d_r > 1;
     vdi_status s = VDI_OK;
     for (int ws = 0; ws <= 3 && s == VDI_OK; ++ws) {
         int occ_max = 1;
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ_max, render_fn(ws, preview), 256, 0);
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ_max, render_fn(ws), 256, 0);
         for (int bps = 1; bps <= std::max(1, occ_max) && s == VDI_OK; ++bps) {
             vdi_batch_opts o = {ws, bps, 0};
             s = render_batch(ctx, reqs, n, &o, st);  // warm-up

@@ -42,6 +42,10 @@ __device__ __forceinline__ void clip_lin(float c0, float c1, float &t0, float &t
 // FP32, except the exact start of rays that cross few lists (FP64, below).
 constexpr float kPreciseSlope = 64.f;  // lists per ray below which list crossings need an FP64 start
 
+// PRECISE_START: the FP64 start for rays that cross few lists (the exact list
+// walk).  The ray-subsampled preview steps between grid cells eight lists
+// apart and places samples in FP32 anyway, so it sets rays up in FP32 only.
+template <bool PRECISE_START = true>
 __device__ __forceinline__ bool setup_ray(const ViewConsts &c, int px, int py, int vw, int vh, Ray &r) {
     if (px < c.rx0 || px > c.rx1 || py < c.ry0 || py > c.ry1) return false;  // outside the box's image
     const float fpx = (float)px, fpy = (float)py;
@@ -110,8 +114,8 @@ __device__ __forceinline__ bool setup_ray(const ViewConsts &c, int px, int py, i
     // angle: an FP32 start coordinate of magnitude w/2 (error ~ w 2^-25) would
     // move its crossings by that error / slope along the ray.  Such rays get
     // their start position relative to the integer origin in FP64.
-    if (((int)floorf(gx1) != ox && fabsf(r.dgx) < kPreciseSlope) ||
-        ((int)floorf(gy1) != oy && fabsf(r.dgy) < kPreciseSlope)) {
+    if (PRECISE_START && (((int)floorf(gx1) != ox && fabsf(r.dgx) < kPreciseSlope) ||
+                          ((int)floorf(gy1) != oy && fabsf(r.dgy) < kPreciseSlope))) {
         // list-grid homogeneous coordinates G(t) = GA + t GB; the position
         // relative to the origin is (G_x - ox G_w) / G_w, whose numerator is
         // c + t d with c, d formed in FP64 before the cancellation

@@ -48,11 +48,17 @@ __device__ __forceinline__ void fill_tiles(const ViewConsts &c, void *out, int o
     }
 }
 
-// The one-list path for views from V_O's eye (PATH 5) waits on its records
-// rather than on arithmetic: it runs with six blocks per SM (register cap)
-// and requests slot pairs two at a time.
+// Resident blocks per SM the register allocation is held to: the one-list
+// path for views from V_O's eye (PATH 5) waits on its records rather than on
+// arithmetic and runs six (it requests slot pairs two at a time); the list
+// walk four (64 registers); the walk with empty-space skipping three.
+template <int PATH>
+struct RenderOccupancy {
+    static constexpr int blocks = PATH == 5 ? 6 : (PATH == 1 ? 3 : 4);
+};
+
 template <int FMT, int MODE, bool ERT, int WX, int PATH>
-__global__ void __launch_bounds__(256, PATH == 5 ? 6 : 1) render_kernel(const ViewConsts c, const DevVdi v, void *out,
+__global__ void __launch_bounds__(256, RenderOccupancy<PATH>::blocks) render_kernel(const ViewConsts c, const DevVdi v, void *out,
                                                      int out_fmt, uint32_t *ray_lists,
                                                      uint32_t *ray_segs) {
     const int nrect = c.tile_w * c.tile_h;
@@ -104,7 +110,7 @@ __global__ void __launch_bounds__(256, 4) preview_kernel(const ViewConsts c, con
     const int px = tx * 32 + (g & 31), py = ty * 8 + unit * ROWS + (g >> 5);
     const bool inside = px < c.W && py < c.H;
     Ray r = {};
-    const bool active = inside && setup_ray(c, px, py, v.w, v.h, r);
+    const bool active = inside && setup_ray<false>(c, px, py, v.w, v.h, r);
     const Accum acc = march_preview_lanes<FMT, kPreviewProbe, L>(v, c, r, active);
     if (inside && (threadIdx.x & (L - 1)) == 0) store_px(out, out_fmt, (size_t)py * c.W + px, acc);
 }
