@@ -16,7 +16,7 @@ import numpy as np
 import pytest
 
 import vdi_synth as S
-from helpers import check_tolerance
+from helpers import check_tolerance, check_with_alternatives
 
 pytestmark = pytest.mark.gpu
 torch = pytest.importorskip("torch")
@@ -90,7 +90,10 @@ def test_render_at_original_view_equals_dvr(V, ctx, orc, name, fmt):
         torch.cuda.synchronize()
         dvr, fl = orc.dvr(orc.Volume(vol, bmin, bmax), kn, cam.view, cam.proj, w, h, step, u, with_flags=True)
         assert dvr[:, 3].max() > 0.3
-        check_tolerance(out.cpu().numpy(), dvr, fmt, mask=fl == 0, what=f"a' {name}")
+        # a ray whose sample count floor(L / step) sits at a rounding boundary has two
+        # valid values; the VDI took the FP32 decision, which the oracle's FP32 DVR repeats
+        dvr32 = orc.dvr(orc.Volume(vol, bmin, bmax), kn, cam.view, cam.proj, w, h, step, u, fp32=True)
+        check_with_alternatives(out.cpu().numpy(), dvr, fmt, fl, dvr32[fl != 0][None], what=f"a' {name}")
     finally:
         V.vdi_destroy(vdi)
 
@@ -157,6 +160,7 @@ def test_adaptive_gamma_bit_exact(V, ctx, orc, name, ns):
         V.vdi_render(vdi, V.camera(cam.view, cam.proj), w, h, 1, 1, out)
         torch.cuda.synchronize()
         dvr, fl = orc.dvr(orc.Volume(vol, bmin, bmax), kn, cam.view, cam.proj, w, h, u, u, with_flags=True)
-        check_tolerance(out.cpu().numpy(), dvr, fmt, mask=fl == 0, what=f"adaptive a' {name}")
+        dvr32 = orc.dvr(orc.Volume(vol, bmin, bmax), kn, cam.view, cam.proj, w, h, u, u, fp32=True)
+        check_with_alternatives(out.cpu().numpy(), dvr, fmt, fl, dvr32[fl != 0][None], what=f"adaptive a' {name}")
     finally:
         V.vdi_destroy(vdi)

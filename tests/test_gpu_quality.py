@@ -11,7 +11,7 @@ import numpy as np
 import pytest
 
 import vdi_synth as S
-from helpers import check_tolerance
+from helpers import check_tolerance, check_with_alternatives
 
 pytestmark = pytest.mark.gpu
 torch = pytest.importorskip("torch")
@@ -48,7 +48,11 @@ def test_dvr_matches_oracle(V, ctx, orc, name, fmt):
         torch.cuda.synchronize()
         ref, fl = orc.dvr(orc.Volume(vol, bmin, bmax), kn, cam.view, cam.proj, W, H, step, u, with_flags=True)
         assert ref[:, 3].max() > 0.3
-        check_tolerance(out.float().cpu().numpy(), ref, fmt, mask=fl == 0, what=f"dvr {name} {az}")
+        # rays whose sample count sits at a rounding boundary: the GPU decides in FP32,
+        # as the oracle's FP32 DVR does
+        ref32 = orc.dvr(orc.Volume(vol, bmin, bmax), kn, cam.view, cam.proj, W, H, step, u, fp32=True)
+        check_with_alternatives(out.float().cpu().numpy(), ref, fmt, fl, ref32[fl != 0][None],
+                                what=f"dvr {name} {az}")
 
 
 @pytest.mark.parametrize("fmt", [0, 1])
