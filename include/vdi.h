@@ -260,9 +260,10 @@ void vdi_pi_destroy(vdi_pi *pi);
 
 /* ---- batched multi-view rendering ---------------------------------------
  * Render up to VDI_BATCH_MAX_REQUESTS views of up to VDI_BATCH_MAX_VDIS
- * resident VDIs (of any resolutions, formats, previews) in one persistent
- * launch: every request is cut into 32x8-pixel tiles, and a grid of
- * (SM count x resident blocks per SM) blocks pulls tiles from one queue.
+ * resident VDIs (of any resolutions, formats, previews) in one batched
+ * launch: exact requests are cut into 32x8-pixel tiles and previews (d_r > 1)
+ * into 32x2-pixel tiles served with four lanes per ray; each kind forms a queue
+ * that a persistent grid of (SM count x resident blocks per SM) blocks drains.
  * Each request renders exactly as vdi_render would (the same per-pixel
  * arithmetic, so results do not depend on what else is in the batch).
  * With use_graph the launch sequence is replayed from a CUDA graph cached per

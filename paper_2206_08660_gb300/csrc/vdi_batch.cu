@@ -1,10 +1,11 @@
 // vdi_batch.cu -- many views of several resident VDIs in one persistent
 // launch, optionally replayed from a CUDA graph, plus the batch autotuner.
 //
-// Every request is cut into 32 x 8 pixel tiles; all tiles of all requests form
-// one queue.  A persistent grid (SM count x resident blocks per SM) pulls tiles
-// from an atomic counter, so requests of different resolutions, previews and
-// VDIs share the GPU without a launch per view.  Requests with image-space
+// Exact requests are cut into 32 x 8 pixel tiles, ray-subsampled previews into
+// 32 x 2 tiles; each kind forms one queue, drained by its own persistent grid
+// (SM count x resident blocks per SM) pulling tiles from an atomic counter, so
+// requests of different resolutions, previews and VDIs share the GPU without a
+// launch per view.  Requests with image-space
 // subsampling (D_I > 1) render into a low-resolution scratch image and a second
 // batched kernel upsamples all of them.  The per-request view constants (ray
 // setup, Section 4.1) travel as kernel parameters, so a captured graph is
@@ -202,7 +203,6 @@ struct BatchPlan {
     size_t scratch_bytes = 0;             // counter + low-resolution images
     std::vector<size_t> lo_offset;        // per request, (size_t)-1 if it renders every pixel
     std::vector<void *> final_out;
-    bool preview = false;                 // some request has d_r > 1
     ~BatchPlan() {
         delete bp;
         delete up;
@@ -252,7 +252,6 @@ static vdi_status plan_batch(vdi_ctx *ctx, const vdi_request *reqs, int n, Batch
         q.vdi = vi;
         q.tiles_x = div_up(Wr, 32);
         if (r.d_r > 1) {  // preview queue: 32 x (8 / kBatchLanes) tiles
-            pl.preview = true;
             q.tile_base = ptiles;
             ptiles += q.tiles_x * div_up(Hr, 8 / kBatchLanes);
             pl.bp->pv_idx[pl.bp->n_pv++] = (unsigned char)i;
