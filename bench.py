@@ -297,6 +297,7 @@ class OracleLeg:
 
 
 SERVING = dict(n_vdis=8, w=1920, h=1080, ns=24, tau=0.01, vol_n=512, rate=240.0, seconds=8.0, replace_every=2.0,
+               high_rate=2000.0, high_seconds=3.0,
                budget=24 << 30, max_batch=32, max_inflight=3,
                res=[(640, 360), (1280, 720), (1280, 720), (1920, 1080)], max_dev=45.0, seed=7)
 
@@ -349,58 +350,66 @@ def serving_leg(V, torch, ctx, dev, cfg=SERVING):
             V.vdi_server_wait(srv, t, 30.0)
             V.vdi_server_release(srv, t)
 
-        # ---- open loop: Poisson arrivals
-        n = int(cfg["rate"] * cfg["seconds"])
-        arrivals = np.cumsum(rng.exponential(1.0 / cfg["rate"], size=n))
-        reqs = make_requests(n)
-        tickets = [None] * n
-        lat, fails = [], 0
-        t_start = time.monotonic()
+        def run_open_loop(rate, seconds, replace):
+            """Poisson arrivals at `rate` requests/s for `seconds`; with `replace`, one
+            slot's VDI is regenerated through the server every replace_every seconds."""
+            n = int(rate * seconds)
+            arrivals = np.cumsum(rng.exponential(1.0 / rate, size=n))
+            reqs = make_requests(n)
+            tickets = [None] * n
+            lat, fails = [], 0
+            st0 = V.vdi_server_stats(srv)
+            t_start = time.monotonic()
 
-        def submitter():
+            def submitter():
+                for i in range(n):
+                    d = t_start + arrivals[i] - time.monotonic()
+                    if d > 0:
+                        time.sleep(d)
+                    slot, cam, W, H, d_i, d_r = reqs[i]
+                    tickets[i] = V.vdi_server_submit(srv, V.view_request(slot, cam, W, H, d_i, d_r))
+
+            def replacer():
+                k = 0
+                while replace and time.monotonic() - t_start < arrivals[-1]:
+                    time.sleep(cfg["replace_every"])
+                    slot = k % cfg["n_vdis"]
+                    # generation through the server: the new VDI's bytes are charged to
+                    # the device budget before it is allocated on the side stream
+                    c = S.orbit_camera(bmin, bmax, cfg["w"] / cfg["h"], az_deg=az0[slot] + 5.0 * (k + 1), el_deg=20.0)
+                    with torch.cuda.stream(side):
+                        V.vdi_server_generate(srv, slot, vol_d, bmin, bmax, kn, V.camera(c.view, c.proj), cfg["w"],
+                                              cfg["h"], cfg["ns"], cfg["tau"], u, u, V.VDI_F16, stream=side)
+                    k += 1
+
+            ts, tr = th.Thread(target=submitter), th.Thread(target=replacer)
+            ts.start()
+            tr.start()
             for i in range(n):
-                d = t_start + arrivals[i] - time.monotonic()
-                if d > 0:
-                    time.sleep(d)
-                slot, cam, W, H, d_i, d_r = reqs[i]
-                tickets[i] = V.vdi_server_submit(srv, V.view_request(slot, cam, W, H, d_i, d_r))
+                while tickets[i] is None:
+                    time.sleep(0.0002)
+                info = V.vdi_server_wait(srv, tickets[i], 30.0)
+                if info.status != 0:
+                    fails += 1
+                else:
+                    lat.append((info.t_done - info.t_submit) * 1e3)
+                V.vdi_server_release(srv, tickets[i])
+            ts.join()
+            tr.join()
+            wall = time.monotonic() - t_start
+            st = V.vdi_server_stats(srv)
+            lat = np.array(lat)
+            return {"offered_rps": rate, "requests": n, "failed": fails,
+                    "p50_ms": float(np.percentile(lat, 50)), "p99_ms": float(np.percentile(lat, 99)),
+                    "throughput_rps": len(lat) / wall,
+                    "mean_batch": (st.batched_requests - st0.batched_requests) / max(st.batches - st0.batches, 1),
+                    "vdi_replacements": int(st.vdi_installs - st0.vdi_installs),
+                    "resident_vdi_bytes_at_end": int(st.vdi_bytes), "budget_bytes": cfg["budget"]}
 
-        def replacer():
-            k = 0
-            while time.monotonic() - t_start < arrivals[-1]:
-                time.sleep(cfg["replace_every"])
-                slot = k % cfg["n_vdis"]
-                # generation through the server: the new VDI's bytes are charged to
-                # the device budget before it is allocated on the side stream
-                c = S.orbit_camera(bmin, bmax, cfg["w"] / cfg["h"], az_deg=az0[slot] + 5.0 * (k + 1), el_deg=20.0)
-                with torch.cuda.stream(side):
-                    V.vdi_server_generate(srv, slot, vol_d, bmin, bmax, kn, V.camera(c.view, c.proj), cfg["w"],
-                                          cfg["h"], cfg["ns"], cfg["tau"], u, u, V.VDI_F16, stream=side)
-                k += 1
-
-        ts, tr = th.Thread(target=submitter), th.Thread(target=replacer)
-        ts.start()
-        tr.start()
-        for i in range(n):
-            while tickets[i] is None:
-                time.sleep(0.0002)
-            info = V.vdi_server_wait(srv, tickets[i], 30.0)
-            if info.status != 0:
-                fails += 1
-            else:
-                lat.append((info.t_done - info.t_submit) * 1e3)
-            V.vdi_server_release(srv, tickets[i])
-        ts.join()
-        tr.join()
-        wall = time.monotonic() - t_start
-        st = V.vdi_server_stats(srv)
-        lat = np.array(lat)
-        open_loop = {"offered_rps": cfg["rate"], "requests": n, "failed": fails,
-                     "p50_ms": float(np.percentile(lat, 50)), "p99_ms": float(np.percentile(lat, 99)),
-                     "throughput_rps": len(lat) / wall, "mean_batch": st.batched_requests / max(st.batches, 1),
-                     "vdi_replacements": int(st.vdi_installs) - cfg["n_vdis"],
-                     "resident_vdi_bytes_at_end": int(st.vdi_bytes), "budget_bytes": cfg["budget"]}
-
+        # ---- open loop: Poisson arrivals at the configured rate, then at a rate near the
+        # server's saturation, where requests that arrive while batches run share launches
+        open_loop = run_open_loop(cfg["rate"], cfg["seconds"], True)
+        open_loop_high = run_open_loop(cfg["high_rate"], cfg["high_seconds"], True)
         # ---- saturated throughput, same request mix: batched server (FP16) ...
         sat = make_requests(512)
         torch.cuda.synchronize()
@@ -447,6 +456,7 @@ def serving_leg(V, torch, ctx, dev, cfg=SERVING):
                         "360p:720p:1080p = 1:2:1, deviation U[0,45] deg, D_I,D_R in {1,2}, one VDI replaced "
                         "every 2 s from a side stream, 24 GB budget",
             "open_loop": open_loop,
+            "open_loop_high_rate": open_loop_high,
             "fp16_vs_fp32_pixel_error": fp16_vs_fp32,
             "saturated": {"batched_fp16_server_rps": batched_rps, "one_view_per_launch_fp32_rps": single_rps,
                           "requests": len(sat)}}
