@@ -83,7 +83,7 @@ def peaks():
 
 def render_kernel_hash() -> str:
     h = hashlib.sha1()
-    for fn in ("vdi_render.cu", "vdi_march.cuh", "vdi_internal.cuh", "vdi_preview.cuh"):
+    for fn in ("vdi_render.cu", "vdi_march.cuh", "vdi_internal.cuh", "vdi_preview.cuh", "vdi_tma.cuh"):
         with open(os.path.join(ROOT, "paper_2206_08660_gb300", "csrc", fn), "rb") as f:
             h.update(f.read())
     return h.hexdigest()[:12]

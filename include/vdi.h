@@ -181,7 +181,12 @@ vdi_status vdi_get_layout(const vdi_t *vdi, vdi_layout *out);
  * a ray passes through; Section 4.2 / Eq. 2: the supersegment pieces it
  * composites; with early termination unless no_ert).  Reading the totals
  * synchronises `stream` (the stream that render was ordered on).  Before any
- * counted frame, frame_recorded is 0 and the totals are 0. */
+ * counted frame, frame_recorded is 0 and the totals are 0.  device_flags:
+ * bits the render kernels set on the device for this VDI, read on every call
+ * (VDI_FLAG_STAGE_TIMEOUT: a bounded wait for a TMA-staged tile of list
+ * records ran out; those rays read global memory instead, so the image is
+ * unaffected, and the flag means the copies were far slower than expected). */
+#define VDI_FLAG_STAGE_TIMEOUT 1u
 typedef struct {
     vdi_layout layout;      /* device bytes by array, grid dims, slots stored per list */
     int w, h, n_s;          /* lists and supersegments per list */
@@ -192,6 +197,7 @@ typedef struct {
     uint64_t rays_hit;      /* rays that passed through at least one list with positive length */
     uint64_t lists;         /* lists passed through with positive length, summed over the rays */
     uint64_t pieces;        /* supersegment pieces of positive length composited, summed over the rays */
+    uint32_t device_flags;  /* VDI_FLAG_* bits set by kernels on this VDI since it was created */
 } vdi_stats_t;
 vdi_status vdi_stats(vdi_t *vdi, vdi_stats_t *out, void *stream);
 

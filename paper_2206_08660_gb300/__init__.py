@@ -18,7 +18,7 @@ import numpy as np
 from . import build as _build
 
 __all__ = [
-    "VDI_F32", "VDI_F16", "VDI_MEM_HOST", "VDI_MEM_DEVICE", "VDI_SEARCH_ALG2", "VDI_SEARCH_BINARY",
+    "VDI_F32", "VDI_F16", "VDI_MEM_HOST", "VDI_MEM_DEVICE", "VDI_SEARCH_ALG2", "VDI_SEARCH_BINARY", "VDI_FLAG_STAGE_TIMEOUT",
     "VDI_SEARCH_LINEAR", "VdiError", "VdiCamera", "VdiDesc", "VdiLayout", "VdiRenderOpts", "load",
     "vdi_ctx_create", "vdi_ctx_destroy", "vdi_layout_bytes", "vdi_create", "vdi_download", "vdi_get_layout", "vdi_stats",
     "vdi_destroy", "vdi_render", "vdi_render_ex", "vdi_render_preview_static", "VDI_STATIC_PREVIEW_PIXELS", "vdi_search_first", "vdi_generate", "vdi_touch_bitmap", "vdi_render_batch", "vdi_autotune_batch", "request",
@@ -31,6 +31,7 @@ VDI_F32, VDI_F16 = 0, 1
 VDI_STATIC_PREVIEW_PIXELS = 524288
 VDI_MEM_HOST, VDI_MEM_DEVICE = 0, 1
 VDI_SEARCH_ALG2, VDI_SEARCH_BINARY, VDI_SEARCH_LINEAR = 0, 1, 2
+VDI_FLAG_STAGE_TIMEOUT = 1
 STATUS = ["VDI_OK", "VDI_ERR_INVALID_ARG", "VDI_ERR_OOM", "VDI_ERR_CUDA", "VDI_ERR_UNSORTED",
           "VDI_ERR_TIMEOUT", "VDI_ERR_BUSY", "VDI_ERR_UNSUPPORTED"]
 
@@ -61,7 +62,8 @@ class VdiLayout(C.Structure):
 class VdiStats(C.Structure):
     _fields_ = [("layout", VdiLayout), ("w", C.c_int), ("h", C.c_int), ("n_s", C.c_int), ("colour_fmt", C.c_int),
                 ("grid_tile", C.c_int), ("frame_recorded", C.c_int), ("frame_w", C.c_int), ("frame_h", C.c_int),
-                ("rays_hit", C.c_uint64), ("lists", C.c_uint64), ("pieces", C.c_uint64)]
+                ("rays_hit", C.c_uint64), ("lists", C.c_uint64), ("pieces", C.c_uint64),
+                ("device_flags", C.c_uint32)]
 
 
 class VdiVolume(C.Structure):

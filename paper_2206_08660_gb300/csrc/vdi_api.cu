@@ -8,18 +8,20 @@
 #include <stdlib.h>
 #include <string.h>
 
+#include <cudaTypedefs.h>
+
+#include <mutex>
 #include <new>
 
 #include "../../include/vdi.h"
 #include "vdi_api_internal.h"
 #include "vdi_internal.cuh"
+#include "vdi_march.cuh"
 
 #define VDI_API extern "C" __attribute__((visibility("default")))
 
 namespace vdi {
 
-cudaError_t launch_render(const ViewConsts &c, const DevVdi &v, void *out, int out_fmt, uint32_t *rl,
-                          uint32_t *rs, int search, int warp_shape, bool ert, bool ess, bool blocks, cudaStream_t st);
 cudaError_t launch_touch(const ViewConsts &c, const DevVdi &v, uint32_t *bm, cudaStream_t st);
 cudaError_t launch_upsample(const float4 *lo, int w0, int h0, void *out, int out_fmt, int W, int H,
                             cudaStream_t st);
@@ -278,6 +280,7 @@ vdi_status make_view_consts(const vdi_t *v, const vdi_camera *cam, int W, int H,
                              ? 1
                              : 0;
     }
+
     for (int k = 0; k < 3; ++k) {
         c->O0[k] = (float)O0[k];
         c->Ox[k] = (float)Ox[k];
@@ -434,6 +437,67 @@ VDI_API vdi_status vdi_get_layout(const vdi_t *v, vdi_layout *out) {
 
 namespace vdi {
 
+// cuTensorMapEncodeTiled from the driver, looked up once through the runtime
+// (no link against the driver library); null when the driver lacks it
+static PFN_cuTensorMapEncodeTiled_v12000 tensor_map_encoder() {
+    static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
+    static std::once_flag once;
+    std::call_once(once, [] {
+        void *p = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) ==
+                cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            fn = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(p);
+        else
+            cudaGetLastError();
+    });
+    return fn;
+}
+
+// Tensor maps of the staged one-list path over a VDI's arrays, all as 32-bit
+// words: ranges (2 w) x h with 32 x 8-list boxes; depth slot pairs and colour
+// records (4 w) x h x planes with boxes of 32 x 8 lists by the staged pairs
+// (staged_pairs: FP16 colour) or twice as many slots (FP32 colour).  They
+// need 16-byte row strides (w even) and 16-byte aligned arrays; false when a
+// condition fails or the driver refuses.
+static bool build_tile_maps(const DevVdi &d, TileMaps *m) {
+    PFN_cuTensorMapEncodeTiled_v12000 enc = tensor_map_encoder();
+    if (!enc || (d.w & 1)) return false;
+    const cuuint32_t np = (cuuint32_t)staged_pairs(d.nsp);
+    if ((reinterpret_cast<uintptr_t>(d.depth) | reinterpret_cast<uintptr_t>(d.colour) |
+         reinterpret_cast<uintptr_t>(d.range)) & 15)
+        return false;
+    const cuuint32_t es[3] = {1, 1, 1};
+    const cuuint64_t w = (cuuint64_t)d.w, h = (cuuint64_t)d.h, plane = (cuuint64_t)d.nl * 16;
+    {
+        const cuuint64_t dim[2] = {2 * w, h}, stride[1] = {w * 8};
+        const cuuint32_t box[2] = {64, 8};
+        if (enc(&m->range, CU_TENSOR_MAP_DATA_TYPE_UINT32, 2, const_cast<float2 *>(d.range), dim, stride, box, es,
+                CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
+            return false;
+    }
+    {
+        const cuuint64_t dim[3] = {4 * w, h, (cuuint64_t)(d.nsp >> 1)}, stride[2] = {w * 16, plane};
+        const cuuint32_t box[3] = {128, 8, np};
+        if (enc(&m->depth, CU_TENSOR_MAP_DATA_TYPE_UINT32, 3, const_cast<float4 *>(d.depth), dim, stride, box, es,
+                CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
+            return false;
+    }
+    {
+        const bool f16 = d.fmt == 1;
+        const cuuint64_t dim[3] = {4 * w, h, (cuuint64_t)(f16 ? (d.nsp >> 1) : d.nsp)}, stride[2] = {w * 16, plane};
+        const cuuint32_t box[3] = {128, 8, f16 ? np : 2 * np};
+        if (enc(&m->colour, CU_TENSOR_MAP_DATA_TYPE_UINT32, 3, const_cast<void *>(d.colour), dim, stride, box, es,
+                CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
+            return false;
+    }
+    return true;
+}
+
 vdi_status alloc_vdi(vdi_ctx *ctx, const vdi_desc *desc, cudaStream_t stream, vdi_t **out) {
     vdi_layout L;
     vdi_status s = check_desc(desc, &L);
@@ -482,12 +546,15 @@ vdi_status alloc_vdi(vdi_ctx *ctx, const vdi_desc *desc, cudaStream_t stream, vd
     if ((e = cudaMallocAsync(&v->depth_mem, L.depth_bytes, stream)) != cudaSuccess ||
         (e = cudaMallocAsync(&v->colour_mem, L.colour_bytes, stream)) != cudaSuccess ||
         (e = cudaMallocAsync((void **)&v->grid_mem, L.grid_bytes, stream)) != cudaSuccess ||
-        (e = cudaMallocAsync((void **)&v->range_mem, L.list_bytes, stream)) != cudaSuccess) {
+        (e = cudaMallocAsync((void **)&v->range_mem, L.list_bytes, stream)) != cudaSuccess ||
+        (e = cudaMallocAsync((void **)&v->status_mem, sizeof(uint32_t), stream)) != cudaSuccess ||
+        (e = cudaMemsetAsync(v->status_mem, 0, sizeof(uint32_t), stream)) != cudaSuccess) {
         vdi_status r = cuda_fail(e, "cudaMallocAsync(VDI)");
         if (v->depth_mem) cudaFreeAsync(v->depth_mem, stream);
         if (v->colour_mem) cudaFreeAsync(v->colour_mem, stream);
         if (v->grid_mem) cudaFreeAsync(v->grid_mem, stream);
         if (v->range_mem) cudaFreeAsync(v->range_mem, stream);
+        if (v->status_mem) cudaFreeAsync(v->status_mem, stream);
         delete v;
         return r;
     }
@@ -499,6 +566,8 @@ vdi_status alloc_vdi(vdi_ctx *ctx, const vdi_desc *desc, cudaStream_t stream, vd
     d.bh = div_up(desc->h, kB);
     v->brange_mem = v->range_mem + d.nl;  // the block ranges follow the list ranges
     d.brange = v->brange_mem;
+    v->maps_ok = build_tile_maps(d, &v->maps) ? 1 : 0;
+    v->maps.status = v->status_mem;
     *out = v;
     return VDI_OK;
 }
@@ -515,6 +584,7 @@ void free_vdi(vdi_t *v) {
     if (v->grid_mem) cudaFreeAsync(v->grid_mem, fs);
     if (v->range_mem) cudaFreeAsync(v->range_mem, fs);
     if (v->totals_mem) cudaFreeAsync(v->totals_mem, fs);
+    if (v->status_mem) cudaFreeAsync(v->status_mem, fs);
     delete v;
 }
 
@@ -661,10 +731,10 @@ VDI_API vdi_status vdi_render_ex(vdi_t *v, const vdi_camera *view, int W, int H,
         CK(cudaMemsetAsync(v->totals_mem, 0, 3 * sizeof(unsigned long long), st));
     }
     if (d_i == 1) {
-        CK(launch_render(c, v->dv, out_rgba, out_fmt, o.ray_lists, o.ray_segs, o.search, ws, !o.no_ert, o.ess != 0, o.blocks != 0, st));
+        CK(launch_render(c, v->dv, out_rgba, out_fmt, o.ray_lists, o.ray_segs, o.search, ws, !o.no_ert, o.ess != 0, o.blocks != 0, tile_maps(v), st));
     } else {
         CK(cudaMallocAsync((void **)&lo, (size_t)Wr * Hr * sizeof(float4), st));
-        CK(launch_render(c, v->dv, lo, VDI_F32, o.ray_lists, o.ray_segs, o.search, ws, !o.no_ert, o.ess != 0, o.blocks != 0, st));
+        CK(launch_render(c, v->dv, lo, VDI_F32, o.ray_lists, o.ray_segs, o.search, ws, !o.no_ert, o.ess != 0, o.blocks != 0, tile_maps(v), st));
         CK(launch_upsample(lo, Wr, Hr, out_rgba, out_fmt, W, H, st));
     }
     if (o.record_stats) {
@@ -692,10 +762,10 @@ VDI_API vdi_status vdi_render_scaled(vdi_t *v, const vdi_camera *view, int W, in
     const int ws = default_warp_shape(c);
     float4 *lo = nullptr;
     if (Wr == W && Hr == H) {
-        CK(launch_render(c, v->dv, out_rgba, out_fmt, nullptr, nullptr, VDI_SEARCH_ALG2, ws, true, false, false, st));
+        CK(launch_render(c, v->dv, out_rgba, out_fmt, nullptr, nullptr, VDI_SEARCH_ALG2, ws, true, false, false, tile_maps(v), st));
     } else {
         CK(cudaMallocAsync((void **)&lo, (size_t)Wr * Hr * sizeof(float4), st));
-        CK(launch_render(c, v->dv, lo, VDI_F32, nullptr, nullptr, VDI_SEARCH_ALG2, ws, true, false, false, st));
+        CK(launch_render(c, v->dv, lo, VDI_F32, nullptr, nullptr, VDI_SEARCH_ALG2, ws, true, false, false, tile_maps(v), st));
         CK(launch_upsample(lo, Wr, Hr, out_rgba, out_fmt, W, H, st));
     }
 done:
@@ -712,10 +782,17 @@ VDI_API vdi_status vdi_stats(vdi_t *v, vdi_stats_t *out, void *stream) {
     s.n_s = v->desc.n_s;
     s.colour_fmt = v->desc.colour_fmt;
     s.grid_tile = v->desc.grid_tile;
+    cudaSetDevice(v->ctx->device);
+    cudaStream_t st = (cudaStream_t)stream;
+    {
+        uint32_t flags = 0;
+        cudaError_t e = cudaMemcpyAsync(&flags, v->status_mem, sizeof flags, cudaMemcpyDeviceToHost, st);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+        if (e != cudaSuccess) return cuda_fail(e, "reading the device status word");
+        s.device_flags = flags;
+    }
     if (v->frame_recorded && v->totals_mem) {
-        cudaSetDevice(v->ctx->device);
         unsigned long long t[3] = {0, 0, 0};
-        cudaStream_t st = (cudaStream_t)stream;
         cudaError_t e = cudaMemcpyAsync(t, v->totals_mem, sizeof t, cudaMemcpyDeviceToHost, st);
         if (e == cudaSuccess) e = cudaStreamSynchronize(st);
         if (e != cudaSuccess) return cuda_fail(e, "reading frame totals");

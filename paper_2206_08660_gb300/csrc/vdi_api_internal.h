@@ -5,6 +5,7 @@
 
 #include "../../include/vdi.h"
 #include "vdi_internal.cuh"
+#include "vdi_tma.cuh"
 
 struct vdi_ctx {
     int device = 0;
@@ -28,6 +29,11 @@ struct vdi_t {
     // frame totals of the last counted render (vdi_stats): rays hit, lists, pieces
     unsigned long long *totals_mem = nullptr;
     int frame_recorded = 0, frame_w = 0, frame_h = 0;
+    uint32_t *status_mem = nullptr;  // device status word (TileMaps::status)
+    // TMA tensor maps over the depth, colour and range arrays (the staged
+    // one-list path); maps_ok = 0 when the layout does not allow them
+    vdi::TileMaps maps{};
+    int maps_ok = 0;
 };
 
 namespace vdi {
@@ -45,6 +51,11 @@ void grid_edges(const double *P, int nz, float *edges);
 size_t touch_words(const vdi_t *v);
 vdi_status check_render_args(const vdi_t *v, int W, int H, int d_i, int d_r, const void *out, int out_fmt);
 void release_batch_cache(vdi_ctx *ctx);
+cudaError_t launch_render(const ViewConsts &c, const DevVdi &v, void *out, int out_fmt, uint32_t *rl, uint32_t *rs,
+                          int search, int warp_shape, bool ert, bool ess, bool blocks, const TileMaps *tm,
+                          cudaStream_t st);
+// the VDI's tensor maps for launch_render, or null when it has none
+inline const TileMaps *tile_maps(const vdi_t *v) { return v->maps_ok ? &v->maps : nullptr; }
 cudaError_t launch_block_range(const DevVdi &v, float2 *brange, cudaStream_t st);
 
 // warp shape used when the caller does not choose one: 4 x 8 pixels per warp

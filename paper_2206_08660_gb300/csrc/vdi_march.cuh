@@ -422,9 +422,31 @@ __device__ __forceinline__ void march_exact(const DevVdi &v, Ray &r, Accum &acc,
 // ---------------------------------------------------------------------------
 constexpr int kSinglePF = 2;  // slot pairs march_single requests at once
 
-template <int FMT, int MODE, bool ERT>
+// The records a 32 x 8 tile of lists holds for the one-list path's first
+// request, as TMA lays them out in shared memory: list ranges, the first
+// kSinglePF depth slot pairs, their colour records (FP16 slot pairs, or FP32
+// slots).  A VDI with fewer slot pairs stages all it has.
+template <int FMT>
+struct StagedTile {
+    float2 range[8][32];
+    float4 depth[kSinglePF][8][32];
+    uint4 colour[(FMT == 1) ? kSinglePF : 2 * kSinglePF][8][32];
+};
+
+// slot pairs a VDI's staged tile holds, and the bytes its TMA requests bring
+__host__ __device__ __forceinline__ int staged_pairs(int nsp) { return min(kSinglePF, nsp >> 1); }
+template <int FMT>
+__host__ __device__ __forceinline__ uint32_t staged_bytes(int nsp) {
+    return (uint32_t)(8 * 32 * sizeof(float2) + (FMT == 1 ? 2 : 3) * staged_pairs(nsp) * 8 * 32 * sizeof(float4));
+}
+
+// STAGED: the list's range and first kSinglePF slot pairs come from the
+// staged tile `st` (origin x0, y0) when it arrived (non-null) and holds the
+// list, else from global memory; the arithmetic does not change.
+template <int FMT, int MODE, bool ERT, bool STAGED = false>
 __device__ __forceinline__ void march_single(const DevVdi &v, Ray &r, Accum &acc, uint32_t &n_lists,
-                                             uint32_t &n_segs) {
+                                             uint32_t &n_segs, const StagedTile<FMT> *st = nullptr, int x0 = 0,
+                                             int y0 = 0) {
     constexpr int PF = kSinglePF;
     const int ox = r.ox, oy = r.oy;
     const float dgx = r.dgx, dgy = r.dgy;
@@ -443,16 +465,28 @@ __device__ __forceinline__ void march_single(const DevVdi &v, Ray &r, Accum &acc
     const int li = iy * v.w + ix;
     const float d_in = fmaf(0.f, g.dz, g.z0), d_out = fmaf(1.f, g.dz, g.z0);
     ++n_lists;
-    const float2 rg = __ldg(v.range + li);
+    const int tlx = ix - x0, tly = iy - y0;
+    const bool in_tile = STAGED && st != nullptr && (unsigned)tlx < 32u && (unsigned)tly < 8u;
     const int npairs = v.nsp >> 1;
+    float2 rg;
     float4 dp[PF];
     uint4 cq[PF];
+    if (in_tile) {  // slots past a short VDI's last pair are read but never used
+        rg = st->range[tly][tlx];
 #pragma unroll
-    for (int k = 0; k < PF; ++k)
-        if (k < npairs) {
-            dp[k] = ld_depth_pair(v, k, li);
-            if (FMT == 1) cq[k] = __ldg(reinterpret_cast<const uint4 *>(v.colour) + (k * v.nl32 + li));
+        for (int k = 0; k < PF; ++k) {
+            dp[k] = st->depth[k][tly][tlx];
+            if (FMT == 1) cq[k] = st->colour[k][tly][tlx];
         }
+    } else {
+        rg = __ldg(v.range + li);
+#pragma unroll
+        for (int k = 0; k < PF; ++k)
+            if (k < npairs) {
+                dp[k] = ld_depth_pair(v, k, li);
+                if (FMT == 1) cq[k] = __ldg(reinterpret_cast<const uint4 *>(v.colour) + (k * v.nl32 + li));
+            }
+    }
     if (d_out < rg.x || d_in > rg.y) return;
     // slots in order; those with b < d_in lie before the first one met (b is
     // sorted).  The records come PF slot pairs at a time: the next PF pairs are
@@ -488,7 +522,14 @@ __device__ __forceinline__ void march_single(const DevVdi &v, Ray &r, Accum &acc
                         cc.k = k0 + k;
                         cc.q = cq[k];
                     }
-                    const float4 col = get_colour<FMT>(cc, v, li, 2 * (k0 + k) + h);
+                    float4 col;
+                    if (FMT == 0 && in_tile && k0 == 0) {
+                        const uint4 q = st->colour[2 * k + h][tly][tlx];
+                        col = make_float4(__uint_as_float(q.x), __uint_as_float(q.y), __uint_as_float(q.z),
+                                          __uint_as_float(q.w));
+                    } else {
+                        col = get_colour<FMT>(cc, v, li, 2 * (k0 + k) + h);
+                    }
                     const float da = fmaf(sa, g.dw, g.w1), db = fmaf(sb, g.dw, g.w1);
                     add_piece(acc, col, g.lw * (sb - sa) * rcp_fast(da * db));
                     ++n_segs;

@@ -22,8 +22,6 @@
 
 namespace vdi {
 
-cudaError_t launch_render(const ViewConsts &c, const DevVdi &v, void *out, int out_fmt, uint32_t *rl, uint32_t *rs,
-                          int search, int warp_shape, bool ert, bool ess, bool blocks, cudaStream_t st);
 cudaError_t launch_upsample(const float4 *lo, int w0, int h0, void *out, int out_fmt, int W, int H,
                             cudaStream_t st);
 
@@ -72,14 +70,14 @@ VDI_API vdi_status vdi_render_preview_static(vdi_t *v, const vdi_camera *view, i
     const int ws = default_warp_shape(c);
     cudaError_t e;
     if (d_i == 1) {
-        e = launch_render(c, v->dv, out_rgba, out_fmt, nullptr, nullptr, VDI_SEARCH_ALG2, ws, true, false, false, st);
+        e = launch_render(c, v->dv, out_rgba, out_fmt, nullptr, nullptr, VDI_SEARCH_ALG2, ws, true, false, false, tile_maps(v), st);
     } else {
         float4 *lo = nullptr;
         st_ = static_preview_buffer(v->ctx->device, &lo);
         if (st_ != VDI_OK) return st_;
         // every low-resolution pixel is written before the upsampling reads it,
         // so nothing left by an earlier call needs clearing
-        e = launch_render(c, v->dv, lo, VDI_F32, nullptr, nullptr, VDI_SEARCH_ALG2, ws, true, false, false, st);
+        e = launch_render(c, v->dv, lo, VDI_F32, nullptr, nullptr, VDI_SEARCH_ALG2, ws, true, false, false, tile_maps(v), st);
         if (e == cudaSuccess) e = launch_upsample(lo, Wr, Hr, out_rgba, out_fmt, W, H, st);
     }
     return e == cudaSuccess ? VDI_OK : cuda_fail(e, "preview render");

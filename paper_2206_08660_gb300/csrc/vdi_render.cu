@@ -18,6 +18,7 @@
 #include "vdi_internal.cuh"
 #include "vdi_march.cuh"
 #include "vdi_preview.cuh"
+#include "vdi_tma.cuh"
 
 namespace vdi {
 
@@ -28,12 +29,36 @@ namespace vdi {
 constexpr int kFillTiles = 8;  // tiles outside the box's pixel rectangle per block
 
 // Fill block fb: kFillTiles tiles outside the box's pixel rectangle, whose
-// rays all miss the box: transparent pixels and zero counters.
+// rays all miss the box: transparent pixels (all-zero bytes in both output
+// formats) and zero counters.  Where every tile row is a 16-byte multiple at
+// a 16-byte boundary, the rows are bulk stores of a zeroed shared-memory row
+// (one per thread of the first two warps); otherwise plain stores.  Every
+// thread of the block must call this.
 __device__ __forceinline__ void fill_tiles(const ViewConsts &c, void *out, int out_fmt, uint32_t *ray_lists,
                                            uint32_t *ray_segs, int fb) {
     const int nrect = c.tile_w * c.tile_h;
     const int ntiles = c.tiles_x * ((c.H + 7) >> 3);
     const int t0 = nrect + fb * kFillTiles, t1 = min(t0 + kFillTiles, ntiles);
+    const bool bulk = ((reinterpret_cast<uintptr_t>(out) & 15) == 0) && (out_fmt == 0 || (c.W & 1) == 0) &&
+                      !ray_lists && !ray_segs;
+    if (bulk) {
+        __shared__ alignas(128) uint4 zero_row[32];  // 32 pixels of FP32 RGBA
+        if (threadIdx.x < 32) zero_row[threadIdx.x] = make_uint4(0u, 0u, 0u, 0u);
+        fence_proxy_async_smem();
+        __syncthreads();
+        const int row = (int)threadIdx.x;  // tile t0 + row / 8, pixel row row % 8 of it
+        if (row < (t1 - t0) * 8) {
+            int tx, ty;
+            tile_of_block(c, t0 + (row >> 3), tx, ty);
+            const int py = ty * 8 + (row & 7), x0 = tx * 32;
+            if (py < c.H && x0 < c.W) {
+                const uint32_t bpp = out_fmt == 0 ? 16u : 8u;
+                bulk_store_wait(reinterpret_cast<char *>(out) + ((size_t)py * c.W + x0) * bpp, zero_row,
+                                (uint32_t)min(32, c.W - x0) * bpp);
+            }
+        }
+        return;
+    }
     const Accum miss = {0.f, 0.f, 0.f, 1.f};
     for (int t = t0; t < t1; ++t) {
         int tx, ty;
@@ -90,6 +115,53 @@ __global__ void __launch_bounds__(256, RenderOccupancy<PATH>::blocks) render_ker
     store_px(out, out_fmt, idx, acc);
     if (ray_lists) ray_lists[idx] = nl;
     if (ray_segs) ray_segs[idx] = nsg;
+}
+
+// Exact path for a view from V_O's eye whose pixel (x, y) lands in list
+// (x, y) (rendering from the original view): each 32 x 8 tile of rays reads
+// one 32 x 8 tile of lists.  One thread requests that tile's list ranges and
+// its first kSinglePF slot pairs (depth and colour) by TMA into shared memory
+// as the block starts, so the copies overlap the ray setup; the rays then
+// take their first records from there (march_single, STAGED) and request the
+// later slot pairs from global memory.  The wait on the copies is bounded:
+// when it runs out, the rays read global memory, the VDI's status word
+// records it, and the block waits again before it exits.
+template <int FMT, int MODE>
+__global__ void __launch_bounds__(256, RenderOccupancy<5>::blocks)
+    staged_single_kernel(const __grid_constant__ TileMaps tm, const ViewConsts c, const DevVdi v, void *out,
+                         int out_fmt) {
+    __shared__ alignas(128) StagedTile<FMT> st;
+    __shared__ uint64_t bar;
+    const int nrect = c.tile_w * c.tile_h;
+    if ((int)blockIdx.x >= nrect) {
+        fill_tiles(c, out, out_fmt, nullptr, nullptr, (int)blockIdx.x - nrect);
+        return;
+    }
+    int tx, ty;
+    tile_of_block(c, blockIdx.x, tx, ty);
+    const int x0 = tx * 32, y0 = ty * 8;
+    if (threadIdx.x == 0) {
+        mbar_init(&bar, 1);
+        mbar_fence_init();
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        mbar_arrive_expect_tx(&bar, staged_bytes<FMT>(v.nsp));
+        tma_load_2d(&st.range[0][0], &tm.range, 2 * x0, y0, &bar);
+        tma_load_3d(&st.depth[0][0][0], &tm.depth, 4 * x0, y0, 0, &bar);
+        tma_load_3d(&st.colour[0][0][0], &tm.colour, 4 * x0, y0, 0, &bar);
+    }
+    const int px = x0 + (int)(threadIdx.x & 31), py = y0 + (int)(threadIdx.x >> 5);
+    const bool inside = px < c.W && py < c.H;
+    Ray r;
+    const bool hit = inside && setup_ray(c, px, py, v.w, v.h, r);
+    const bool ready = mbar_wait(&bar, 0);
+    if (!ready) atomicOr(tm.status, kStatusStageTimeout);
+    Accum acc = {0.f, 0.f, 0.f, 1.f};
+    uint32_t nl = 0, nsg = 0;
+    if (hit) march_single<FMT, MODE, true, true>(v, r, acc, nl, nsg, ready ? &st : nullptr, x0, y0);
+    if (inside) store_px(out, out_fmt, (size_t)py * c.W + px, acc);
+    if (!ready) mbar_wait(&bar, 0);  // no copy into this block's shared memory may outlive it
 }
 
 // Ray-subsampled preview (Section 4.4) with L lanes per ray: the blocks of a
@@ -260,9 +332,38 @@ static cudaError_t launch_ws(const ViewConsts &c, const DevVdi &v, void *out, in
     return cudaGetLastError();
 }
 
+// A view from V_O's eye renders the original image when pixel (x, y)'s ray
+// lands in list (x, y): then a 32 x 8 tile of rays reads one 32 x 8 tile of
+// lists, which the staged kernel loads by TMA.  The ray's list position is
+// GB / GB_w (GA vanishes for such a view); a projective map that keeps the
+// four corner pixel centres within a quarter list of their own list centres
+// keeps every pixel in its list.  (Only the speed depends on this: a ray
+// whose list lies outside its tile reads global memory.)
+static bool stage_tiles(const ViewConsts &c, const DevVdi &v) {
+    if (!c.single_list || c.d_r != 1 || c.W != v.w || c.H != v.h) return false;
+    for (int corner = 0; corner < 4; ++corner) {
+        const double px = (corner & 1) ? c.W - 1 : 0, py = (corner & 2) ? c.H - 1 : 0;
+        double g[3];
+        for (int k = 0; k < 3; ++k) g[k] = c.GB0[k] + px * c.GBx[k] + py * c.GBy[k];
+        if (!(g[2] > 0.0) || !(fabs(g[0] / g[2] - (px + 0.5)) < 0.25) || !(fabs(g[1] / g[2] - (py + 0.5)) < 0.25))
+            return false;
+    }
+    return true;
+}
+
+template <int FMT>
+static cudaError_t launch_staged(const TileMaps &tm, const ViewConsts &c, const DevVdi &v, void *out, int out_fmt,
+                                 cudaStream_t st) {
+    const int nrect = c.tile_w * c.tile_h, ntiles = div_up(c.W, 32) * div_up(c.H, 8);
+    staged_single_kernel<FMT, kSearchAlg2>
+        <<<nrect + div_up(ntiles - nrect, kFillTiles), 256, 0, st>>>(tm, c, v, out, out_fmt);
+    return cudaGetLastError();
+}
+
 template <int FMT, int MODE>
 static cudaError_t launch_m(const ViewConsts &c, const DevVdi &v, void *out, int out_fmt, uint32_t *rl,
-                            uint32_t *rs, int warp_shape, bool ert, bool ess, bool blocks, cudaStream_t st) {
+                            uint32_t *rs, int warp_shape, bool ert, bool ess, bool blocks, const TileMaps *tm,
+                            cudaStream_t st) {
     if (c.d_r > 1) {
         // previews ignore the search mode and the warp shape (their samples use
         // a wide probe, several lanes serve a ray); their counters stay zero
@@ -274,26 +375,29 @@ static cudaError_t launch_m(const ViewConsts &c, const DevVdi &v, void *out, int
     if (!ert) return launch_ws<FMT, MODE, false, 0>(c, v, out, out_fmt, rl, rs, warp_shape, st);
     if (rl || rs) return launch_ws<FMT, MODE, true, 0>(c, v, out, out_fmt, rl, rs, warp_shape, st);
     if (ess) return launch_ws<FMT, MODE, true, 1>(c, v, out, out_fmt, rl, rs, warp_shape, st);
-    if (!blocks && c.single_list && MODE == kSearchAlg2)
+    if (!blocks && c.single_list && MODE == kSearchAlg2) {
+        if (tm && stage_tiles(c, v)) return launch_staged<FMT>(*tm, c, v, out, out_fmt, st);
         return launch_ws<FMT, MODE, true, 5>(c, v, out, out_fmt, rl, rs, warp_shape, st);
+    }
     if (!blocks) return launch_ws<FMT, MODE, true, 0>(c, v, out, out_fmt, rl, rs, warp_shape, st);
     return launch_ws<FMT, MODE, true, 3>(c, v, out, out_fmt, rl, rs, warp_shape, st);
 }
 
 cudaError_t launch_render(const ViewConsts &c, const DevVdi &v, void *out, int out_fmt, uint32_t *rl, uint32_t *rs,
-                          int search, int warp_shape, bool ert, bool ess, bool blocks, cudaStream_t st) {
+                          int search, int warp_shape, bool ert, bool ess, bool blocks, const TileMaps *tm,
+                          cudaStream_t st) {
     if (v.fmt == 0) {
         if (search == kSearchBinary)
-            return launch_m<0, kSearchBinary>(c, v, out, out_fmt, rl, rs, warp_shape, ert, ess, blocks, st);
+            return launch_m<0, kSearchBinary>(c, v, out, out_fmt, rl, rs, warp_shape, ert, ess, blocks, tm, st);
         if (search == kSearchLinear)
-            return launch_m<0, kSearchLinear>(c, v, out, out_fmt, rl, rs, warp_shape, ert, ess, blocks, st);
-        return launch_m<0, kSearchAlg2>(c, v, out, out_fmt, rl, rs, warp_shape, ert, ess, blocks, st);
+            return launch_m<0, kSearchLinear>(c, v, out, out_fmt, rl, rs, warp_shape, ert, ess, blocks, tm, st);
+        return launch_m<0, kSearchAlg2>(c, v, out, out_fmt, rl, rs, warp_shape, ert, ess, blocks, tm, st);
     }
     if (search == kSearchBinary)
-        return launch_m<1, kSearchBinary>(c, v, out, out_fmt, rl, rs, warp_shape, ert, ess, blocks, st);
+        return launch_m<1, kSearchBinary>(c, v, out, out_fmt, rl, rs, warp_shape, ert, ess, blocks, tm, st);
     if (search == kSearchLinear)
-        return launch_m<1, kSearchLinear>(c, v, out, out_fmt, rl, rs, warp_shape, ert, ess, blocks, st);
-    return launch_m<1, kSearchAlg2>(c, v, out, out_fmt, rl, rs, warp_shape, ert, ess, blocks, st);
+        return launch_m<1, kSearchLinear>(c, v, out, out_fmt, rl, rs, warp_shape, ert, ess, blocks, tm, st);
+    return launch_m<1, kSearchAlg2>(c, v, out, out_fmt, rl, rs, warp_shape, ert, ess, blocks, tm, st);
 }
 
 cudaError_t launch_upsample(const float4 *lo, int w0, int h0, void *out, int out_fmt, int W, int H,

@@ -338,6 +338,38 @@ def test_views_from_the_original_eye(V, ctx, orc, fmt, zoom, ns):
         V.vdi_destroy(vdi)
 
 
+@pytest.mark.parametrize("w,h,ns,fmt", [(70, 27, 9, 1), (70, 27, 20, 0), (70, 27, 20, 1), (64, 16, 4, 1),
+                                         (64, 16, 4, 0), (45, 27, 9, 1), (70, 27, 2, 1)])
+def test_original_view_with_staged_tiles(V, ctx, orc, w, h, ns, fmt):
+    """Rendering from V_O's own camera at the VDI's resolution: pixel (x, y)'s
+    ray stays in list (x, y), so each 32 x 8 tile of rays reads one 32 x 8
+    tile of lists, whose ranges and first slot pairs the one-list path loads
+    into shared memory by TMA (even w; w = 45 takes the unstaged one-list
+    path).  Ragged tiles on the right and bottom edges; N_S = 2, 4 (fewer slot
+    pairs than a tile stages), 9 and 20 (slot pairs beyond the staged ones
+    from global memory); FP32 and FP16 colour.  The image is bit-identical to
+    the general list walk, matches the oracle, and its FP16 output is the
+    FP32 output rounded; no wait for a staged tile ran out."""
+    case = random_case(w, h, ns, seed=5, u=0.15, alpha_range=(0.05, 0.8), fill=0.9)
+    sc = case.oracle_scene(orc)
+    vdi = V.vdi_create(ctx, case.gpu_desc(V, fmt), case.vdi.rgba, case.vdi.depth, case.vdi.counts)
+    try:
+        cn = case.cam_o
+        fast = gpu_render(V, vdi, cn, w, h)
+        walk, _, _ = gpu_render(V, vdi, cn, w, h, counters=True)
+        assert np.array_equal(fast, walk)
+        half = torch.zeros((h, w, 4), dtype=torch.float16, device="cuda")
+        V.vdi_render(vdi, V.camera(cn.view, cn.proj), w, h, 1, 1, half, V.VDI_F16)
+        torch.cuda.synchronize()
+        assert np.array_equal(half.cpu().numpy().reshape(-1, 4), fast.astype(np.float16))
+        ref, _, _, fl = orc.render_exact(sc, cn.view, cn.proj, w, h)
+        assert ref[:, 3].max() > 0.3
+        check_exact(orc, sc, cn, w, h, fast, fmt, ref, fl, what=f"original view {w}x{h} N_S={ns}")
+        assert V.vdi_stats(vdi).device_flags == 0
+    finally:
+        V.vdi_destroy(vdi)
+
+
 @pytest.mark.parametrize("zoom,shift", [(0.35, 0.0), (1.0, 0.45), (0.35, 3.0)])
 def test_tiles_outside_the_box_image(V, ctx, orc, zoom, shift):
     """The render grid dispatches the tiles that meet the box's pixel
