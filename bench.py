@@ -371,8 +371,12 @@ def serving_leg(V, torch, ctx, dev, cfg=SERVING):
 
             def replacer():
                 k = 0
-                while replace and time.monotonic() - t_start < arrivals[-1]:
-                    time.sleep(cfg["replace_every"])
+                while replace:
+                    # one replacement every replace_every seconds while requests still arrive
+                    t_next = t_start + (k + 1) * cfg["replace_every"]
+                    if t_next - t_start >= arrivals[-1]:
+                        break
+                    time.sleep(max(0.0, t_next - time.monotonic()))
                     slot = k % cfg["n_vdis"]
                     # generation through the server: the new VDI's bytes are charged to
                     # the device budget before it is allocated on the side stream
@@ -394,9 +398,9 @@ def serving_leg(V, torch, ctx, dev, cfg=SERVING):
                 else:
                     lat.append((info.t_done - info.t_submit) * 1e3)
                 V.vdi_server_release(srv, tickets[i])
+            wall = time.monotonic() - t_start  # first arrival to the last result read
             ts.join()
             tr.join()
-            wall = time.monotonic() - t_start
             st = V.vdi_server_stats(srv)
             lat = np.array(lat)
             return {"offered_rps": rate, "requests": n, "failed": fails,

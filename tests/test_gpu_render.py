@@ -370,19 +370,23 @@ def test_original_view_with_staged_tiles(V, ctx, orc, w, h, ns, fmt):
         V.vdi_destroy(vdi)
 
 
-@pytest.mark.parametrize("zoom,shift", [(0.35, 0.0), (1.0, 0.45), (0.35, 3.0)])
-def test_tiles_outside_the_box_image(V, ctx, orc, zoom, shift):
+@pytest.mark.parametrize("zoom,shift,W", [(0.35, 0.0, 203), (1.0, 0.45, 203), (0.35, 3.0, 203), (0.35, 0.0, 204),
+                                          (1.0, 0.45, 204)])
+def test_tiles_outside_the_box_image(V, ctx, orc, zoom, shift, W):
     """The render grid dispatches the tiles that meet the box's pixel
     rectangle first and clears the others in blocks of several tiles: with the
     box small on screen, cut by the image's left and bottom edges, or out of
     the view entirely (look-at point moved sideways by shift times the eye's
     distance), every pixel and both per-ray counters still match the oracle;
-    the cleared pixels are transparent and their counters zero."""
+    the cleared pixels are transparent and their counters zero.  The clearing
+    uses bulk stores where every row is 16-byte aligned (FP32 output, FP16
+    output at an even width) and plain stores otherwise (counters, FP16 at an
+    odd width): the FP16 image is the FP32 one rounded either way."""
     case = random_case(31, 19, 4, seed=21, u=0.2, alpha_range=(0.05, 0.8))
     sc = case.oracle_scene(orc)
     vdi = V.vdi_create(ctx, case.gpu_desc(V, 1), case.vdi.rgba, case.vdi.depth, case.vdi.counts)
     try:
-        W, H = 203, 91  # 7 x 12 tiles with ragged edges
+        H = 91  # 7 x 12 tiles with ragged edges
         cn = S.orbit_camera(case.bmin, case.bmax, W / H, az_deg=12.0, el_deg=10.0, zoom=zoom)
         if shift:
             centre = 0.5 * (np.asarray(case.bmin) + np.asarray(case.bmax))
@@ -399,6 +403,10 @@ def test_tiles_outside_the_box_image(V, ctx, orc, zoom, shift):
         torch.cuda.synchronize()
         got = out.cpu().numpy().reshape(-1, 4)
         assert np.array_equal(got, fast.cpu().numpy().reshape(-1, 4))
+        half = torch.full((H, W, 4), 7.0, dtype=torch.float16, device="cuda")
+        V.vdi_render(vdi, V.camera(cn.view, cn.proj), W, H, 1, 1, half, V.VDI_F16)
+        torch.cuda.synchronize()
+        assert np.array_equal(half.cpu().numpy().reshape(-1, 4), got.astype(np.float16))
         ok = fl == 0
         check_exact(orc, sc, cn, W, H, got, 1, ref, fl, what=f"shift {shift}")
         assert np.array_equal(rl.cpu().numpy().reshape(-1)[ok], lists[ok])
