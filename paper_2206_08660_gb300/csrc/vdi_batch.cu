@@ -163,27 +163,16 @@ __global__ void __launch_bounds__(256) batch_upsample_kernel(const UpParams P) {
     }
     const UpReq &q = P.reqs[lo];
     const int local = tile - q.tile_base;
-    const int X = (local % q.tiles_x) * 32 + (threadIdx.x & 31);
+    const int X0 = (local % q.tiles_x) * (32 * kUpPixels) + (threadIdx.x & 31);
     const int Y = (local / q.tiles_x) * 8 + (threadIdx.x >> 5);
-    if (X >= q.W || Y >= q.H) return;
-    const float u = ((float)X + 0.5f) * ((float)q.w0 / (float)q.W) - 0.5f;
-    const float vv = ((float)Y + 0.5f) * ((float)q.h0 / (float)q.H) - 0.5f;
-    const int i0 = (int)floorf(u), j0 = (int)floorf(vv);
-    const float fu = u - (float)i0, fv = vv - (float)j0;
-    const int i1 = min(max(i0 + 1, 0), q.w0 - 1), j1 = min(max(j0 + 1, 0), q.h0 - 1);
-    const int ic = min(max(i0, 0), q.w0 - 1), jc = min(max(j0, 0), q.h0 - 1);
-    const float4 a = __ldg(q.lo + (size_t)jc * q.w0 + ic), b = __ldg(q.lo + (size_t)jc * q.w0 + i1);
-    const float4 d = __ldg(q.lo + (size_t)j1 * q.w0 + ic), e = __ldg(q.lo + (size_t)j1 * q.w0 + i1);
-    const float4 top = make_float4(fmaf(fu, b.x - a.x, a.x), fmaf(fu, b.y - a.y, a.y), fmaf(fu, b.z - a.z, a.z),
-                                   fmaf(fu, b.w - a.w, a.w));
-    const float4 bot = make_float4(fmaf(fu, e.x - d.x, d.x), fmaf(fu, e.y - d.y, d.y), fmaf(fu, e.z - d.z, d.z),
-                                   fmaf(fu, e.w - d.w, d.w));
-    Accum acc;
-    acc.r = fmaf(fv, bot.x - top.x, top.x);
-    acc.g = fmaf(fv, bot.y - top.y, top.y);
-    acc.b = fmaf(fv, bot.z - top.z, top.z);
-    acc.T = 1.f - fmaf(fv, bot.w - top.w, top.w);
-    store_px(q.out, q.out_fmt, (size_t)Y * q.W + X, acc);
+    if (Y >= q.H) return;
+    Accum acc[kUpPixels];
+#pragma unroll
+    for (int k = 0; k < kUpPixels; ++k)
+        if (X0 + 32 * k < q.W) acc[k] = upsample_px(q.lo, q.w0, q.h0, q.W, q.H, X0 + 32 * k, Y);
+#pragma unroll
+    for (int k = 0; k < kUpPixels; ++k)
+        if (X0 + 32 * k < q.W) store_px(q.out, q.out_fmt, (size_t)Y * q.W + X0 + 32 * k, acc[k]);
 }
 
 static const void *render_fn(int ws) {
@@ -275,7 +264,7 @@ static vdi_status plan_batch(vdi_ctx *ctx, const vdi_request *reqs, int n, Batch
             u.W = r.W;
             u.H = r.H;
             u.out_fmt = r.out_fmt;
-            u.tiles_x = div_up(r.W, 32);
+            u.tiles_x = div_up(r.W, 32 * kUpPixels);
             u.tile_base = up_tiles;
             up_tiles += u.tiles_x * div_up(r.H, 8);
         }

@@ -694,6 +694,35 @@ __device__ __forceinline__ void tile_of_block(const ViewConsts &c, int b, int &t
     tx = k - r * c.tiles_x;
 }
 
+// Bilinear upsampling of a D_I preview (Section 4.4): output pixel (X, Y) of
+// a W x H image from the w0 x h0 low-resolution one, half-pixel centres,
+// clamp to edge.  The upsampling kernels give each thread kUpPixels output
+// pixels 32 apart in x (stores stay coalesced; a thread has that many
+// independent load chains).
+constexpr int kUpPixels = 2;
+
+__device__ __forceinline__ Accum upsample_px(const float4 *__restrict__ lo, int w0, int h0, int W, int H, int X,
+                                             int Y) {
+    const float u = ((float)X + 0.5f) * ((float)w0 / (float)W) - 0.5f;
+    const float vv = ((float)Y + 0.5f) * ((float)h0 / (float)H) - 0.5f;
+    const int i0 = (int)floorf(u), j0 = (int)floorf(vv);
+    const float fu = u - (float)i0, fv = vv - (float)j0;
+    const int i1 = min(max(i0 + 1, 0), w0 - 1), j1 = min(max(j0 + 1, 0), h0 - 1);
+    const int ic = min(max(i0, 0), w0 - 1), jc = min(max(j0, 0), h0 - 1);
+    const float4 a = __ldg(lo + (size_t)jc * w0 + ic), b = __ldg(lo + (size_t)jc * w0 + i1);
+    const float4 d = __ldg(lo + (size_t)j1 * w0 + ic), e = __ldg(lo + (size_t)j1 * w0 + i1);
+    const float4 top = make_float4(fmaf(fu, b.x - a.x, a.x), fmaf(fu, b.y - a.y, a.y), fmaf(fu, b.z - a.z, a.z),
+                                   fmaf(fu, b.w - a.w, a.w));
+    const float4 bot = make_float4(fmaf(fu, e.x - d.x, d.x), fmaf(fu, e.y - d.y, d.y), fmaf(fu, e.z - d.z, d.z),
+                                   fmaf(fu, e.w - d.w, d.w));
+    Accum acc;
+    acc.r = fmaf(fv, bot.x - top.x, top.x);
+    acc.g = fmaf(fv, bot.y - top.y, top.y);
+    acc.b = fmaf(fv, bot.z - top.z, top.z);
+    acc.T = 1.f - fmaf(fv, bot.w - top.w, top.w);
+    return acc;
+}
+
 __device__ __forceinline__ void store_px(void *out, int out_fmt, size_t idx, const Accum &acc) {
     const float a = 1.f - acc.T;
     if (out_fmt == 0) {

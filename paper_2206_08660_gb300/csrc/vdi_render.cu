@@ -226,30 +226,20 @@ cudaError_t launch_touch(const ViewConsts &c, const DevVdi &v, uint32_t *bm, cud
     return cudaGetLastError();
 }
 
-// Bilinear upsampling of the D_I preview: half-pixel centres, clamp to edge.
-__global__ void upsample_kernel(const float4 *__restrict__ lo, int w0, int h0, void *out, int out_fmt,
-                                int W, int H) {
-    const int X = blockIdx.x * blockDim.x + threadIdx.x;
+// Bilinear upsampling of the D_I preview (upsample_px): a 32 x 8 block
+// covers 32 kUpPixels x 8 output pixels.
+__global__ void __launch_bounds__(256) upsample_kernel(const float4 *__restrict__ lo, int w0, int h0, void *out,
+                                                        int out_fmt, int W, int H) {
     const int Y = blockIdx.y * blockDim.y + threadIdx.y;
-    if (X >= W || Y >= H) return;
-    const float u = ((float)X + 0.5f) * ((float)w0 / (float)W) - 0.5f;
-    const float vv = ((float)Y + 0.5f) * ((float)h0 / (float)H) - 0.5f;
-    const int i0 = (int)floorf(u), j0 = (int)floorf(vv);
-    const float fu = u - (float)i0, fv = vv - (float)j0;
-    const int i1 = min(max(i0 + 1, 0), w0 - 1), j1 = min(max(j0 + 1, 0), h0 - 1);
-    const int ic = min(max(i0, 0), w0 - 1), jc = min(max(j0, 0), h0 - 1);
-    const float4 a = __ldg(lo + (size_t)jc * w0 + ic), b = __ldg(lo + (size_t)jc * w0 + i1);
-    const float4 d = __ldg(lo + (size_t)j1 * w0 + ic), e = __ldg(lo + (size_t)j1 * w0 + i1);
-    Accum acc;
-    float4 top = make_float4(fmaf(fu, b.x - a.x, a.x), fmaf(fu, b.y - a.y, a.y), fmaf(fu, b.z - a.z, a.z),
-                             fmaf(fu, b.w - a.w, a.w));
-    float4 bot = make_float4(fmaf(fu, e.x - d.x, d.x), fmaf(fu, e.y - d.y, d.y), fmaf(fu, e.z - d.z, d.z),
-                             fmaf(fu, e.w - d.w, d.w));
-    acc.r = fmaf(fv, bot.x - top.x, top.x);
-    acc.g = fmaf(fv, bot.y - top.y, top.y);
-    acc.b = fmaf(fv, bot.z - top.z, top.z);
-    acc.T = 1.f - fmaf(fv, bot.w - top.w, top.w);
-    store_px(out, out_fmt, (size_t)Y * W + X, acc);
+    if (Y >= H) return;
+    const int X0 = blockIdx.x * (32 * kUpPixels) + threadIdx.x;
+    Accum acc[kUpPixels];
+#pragma unroll
+    for (int k = 0; k < kUpPixels; ++k)
+        if (X0 + 32 * k < W) acc[k] = upsample_px(lo, w0, h0, W, H, X0 + 32 * k, Y);
+#pragma unroll
+    for (int k = 0; k < kUpPixels; ++k)
+        if (X0 + 32 * k < W) store_px(out, out_fmt, (size_t)Y * W + X0 + 32 * k, acc[k]);
 }
 
 // First-supersegment search on one list for a batch of queries (diagnostic).
@@ -402,7 +392,7 @@ cudaError_t launch_render(const ViewConsts &c, const DevVdi &v, void *out, int o
 
 cudaError_t launch_upsample(const float4 *lo, int w0, int h0, void *out, int out_fmt, int W, int H,
                             cudaStream_t st) {
-    dim3 block(32, 8), grid(div_up(W, 32), div_up(H, 8));
+    dim3 block(32, 8), grid(div_up(W, 32 * kUpPixels), div_up(H, 8));
     upsample_kernel<<<grid, block, 0, st>>>(lo, w0, h0, out, out_fmt, W, H);
     return cudaGetLastError();
 }
