@@ -339,13 +339,14 @@ def test_views_from_the_original_eye(V, ctx, orc, fmt, zoom, ns):
 
 
 @pytest.mark.parametrize("w,h,ns,fmt", [(70, 27, 9, 1), (70, 27, 20, 0), (70, 27, 20, 1), (64, 16, 4, 1),
-                                         (64, 16, 4, 0), (45, 27, 9, 1), (70, 27, 2, 1)])
+                                         (64, 16, 4, 0), (45, 27, 9, 1), (70, 27, 2, 1), (16, 6, 4, 1)])
 def test_original_view_with_staged_tiles(V, ctx, orc, w, h, ns, fmt):
     """Rendering from V_O's own camera at the VDI's resolution: pixel (x, y)'s
     ray stays in list (x, y), so each 32 x 8 tile of rays reads one 32 x 8
     tile of lists, whose ranges and first slot pairs the one-list path loads
     into shared memory by TMA (even w; w = 45 takes the unstaged one-list
-    path).  Ragged tiles on the right and bottom edges; N_S = 2, 4 (fewer slot
+    path).  Ragged tiles on the right and bottom edges, and a 16 x 6 VDI
+    smaller than one tile; N_S = 2, 4 (fewer slot
     pairs than a tile stages), 9 and 20 (slot pairs beyond the staged ones
     from global memory); FP32 and FP16 colour.  The image is bit-identical to
     the general list walk, matches the oracle, and its FP16 output is the
