@@ -104,7 +104,10 @@ typedef struct {
     int no_ert;          /* 1: keep compositing past full opacity (for exact counters) */
     uint32_t *ray_lists; /* nullable device [H'][W']: lists traversed with positive length per ray */
     uint32_t *ray_segs;  /* nullable device [H'][W']: supersegment pieces of positive length per ray */
-    int warp_shape;      /* -1: default (32x1 for exact renders from V_O's eye, else 4x8); 0: 32x1, 1: 16x2, 2: 8x4, 3: 4x8 pixels per warp */
+    int warp_shape;      /* -1: default (32x1 for exact renders from V_O's eye, else 4x8); 0: 32x1, 1: 16x2, 2: 8x4, 3: 4x8 pixels per warp.
+                            A view from V_O's eye at V_O's own pixel grid with 32x1 warps loads each
+                            32x8 tile's list ranges and first slot pairs into shared memory by TMA;
+                            the image does not depend on the shape. */
     int ess;             /* 1: empty-space skipping over the count grid (Section 4.3): occupied cells
                             only.  Off by default (measured slower on the benchmark workloads); the
                             image is the same up to where early termination lands; per-ray

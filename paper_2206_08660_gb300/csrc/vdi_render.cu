@@ -366,7 +366,9 @@ static cudaError_t launch_m(const ViewConsts &c, const DevVdi &v, void *out, int
     if (rl || rs) return launch_ws<FMT, MODE, true, 0>(c, v, out, out_fmt, rl, rs, warp_shape, st);
     if (ess) return launch_ws<FMT, MODE, true, 1>(c, v, out, out_fmt, rl, rs, warp_shape, st);
     if (!blocks && c.single_list && MODE == kSearchAlg2) {
-        if (tm && stage_tiles(c, v)) return launch_staged<FMT>(*tm, c, v, out, out_fmt, st);
+        // the staged kernel's warps cover 32 x 1 pixels (the default here); another
+        // requested shape takes the unstaged one-list kernel with that shape
+        if (tm && warp_shape == 0 && stage_tiles(c, v)) return launch_staged<FMT>(*tm, c, v, out, out_fmt, st);
         return launch_ws<FMT, MODE, true, 5>(c, v, out, out_fmt, rl, rs, warp_shape, st);
     }
     if (!blocks) return launch_ws<FMT, MODE, true, 0>(c, v, out, out_fmt, rl, rs, warp_shape, st);

@@ -350,7 +350,8 @@ def test_original_view_with_staged_tiles(V, ctx, orc, w, h, ns, fmt):
     pairs than a tile stages), 9 and 20 (slot pairs beyond the staged ones
     from global memory); FP32 and FP16 colour.  The image is bit-identical to
     the general list walk, matches the oracle, and its FP16 output is the
-    FP32 output rounded; no wait for a staged tile ran out."""
+    FP32 output rounded, and 4 x 8 warps (the unstaged kernel) give the same
+    image; no wait for a staged tile ran out."""
     case = random_case(w, h, ns, seed=5, u=0.15, alpha_range=(0.05, 0.8), fill=0.9)
     sc = case.oracle_scene(orc)
     vdi = V.vdi_create(ctx, case.gpu_desc(V, fmt), case.vdi.rgba, case.vdi.depth, case.vdi.counts)
@@ -359,6 +360,8 @@ def test_original_view_with_staged_tiles(V, ctx, orc, w, h, ns, fmt):
         fast = gpu_render(V, vdi, cn, w, h)
         walk, _, _ = gpu_render(V, vdi, cn, w, h, counters=True)
         assert np.array_equal(fast, walk)
+        # 4 x 8 warps take the unstaged one-list kernel: the same image
+        assert np.array_equal(gpu_render(V, vdi, cn, w, h, warp_shape=3), fast)
         half = torch.zeros((h, w, 4), dtype=torch.float16, device="cuda")
         V.vdi_render(vdi, V.camera(cn.view, cn.proj), w, h, 1, 1, half, V.VDI_F16)
         torch.cuda.synchronize()
