@@ -94,3 +94,41 @@ def test_layout_rejects_bad_descriptors():
         assert e.value.status == 1
     # odd N_S is stored rounded up to even
     assert V.vdi_layout_bytes(V.desc(8, 8, 5, np.eye(4), np.eye(4), (0, 0, 0), (1, 1, 1), 1.0)).n_s_stored == 6
+
+
+def test_ctypes_structures_match_the_header(tmp_path):
+    """Every structure the binding passes across the ABI has the header's
+    layout: a C program built against include/vdi.h prints the size of each
+    struct and the offset of each field, and the ctypes mirrors must agree."""
+    import shutil
+    import subprocess
+
+    import paper_2206_08660_gb300 as V
+
+    cc = shutil.which("gcc") or shutil.which("cc")
+    if cc is None:
+        pytest.skip("no C compiler")
+    pairs = [("vdi_camera", V.VdiCamera), ("vdi_desc", V.VdiDesc), ("vdi_layout", V.VdiLayout),
+             ("vdi_stats_t", V.VdiStats), ("vdi_volume", V.VdiVolume), ("vdi_tf", V.VdiTf),
+             ("vdi_gen_params", V.VdiGenParams), ("vdi_request", V.VdiRequest), ("vdi_batch_opts", V.VdiBatchOpts),
+             ("vdi_server_config", V.VdiServerConfig), ("vdi_view_request", V.VdiViewRequest),
+             ("vdi_ticket_info", V.VdiTicketInfo), ("vdi_server_counters", V.VdiServerCounters),
+             ("vdi_render_opts", V.VdiRenderOpts), ("vdi_pi_config", V.VdiPiConfig)]
+    lines = ['#include <stdio.h>', '#include <stddef.h>', '#include "vdi.h"', "int main(void) {"]
+    for cname, py in pairs:
+        lines.append(f'    printf("{cname} size %zu\\n", sizeof({cname}));')
+        for fname, _ in py._fields_:
+            lines.append(f'    printf("{cname} {fname} %zu\\n", offsetof({cname}, {fname}));')
+    lines += ["    return 0;", "}"]
+    src = tmp_path / "layout.c"
+    src.write_text("\n".join(lines) + "\n")
+    exe = tmp_path / "layout"
+    subprocess.run([cc, "-std=c11", "-I", os.path.join(ROOT, "include"), str(src), "-o", str(exe)], check=True)
+    got = {}
+    for line in subprocess.run([str(exe)], check=True, capture_output=True, text=True).stdout.splitlines():
+        name, field, value = line.split()
+        got[(name, field)] = int(value)
+    for cname, py in pairs:
+        assert got[(cname, "size")] == C.sizeof(py), cname
+        for fname, _ in py._fields_:
+            assert got[(cname, fname)] == getattr(py, fname).offset, (cname, fname)
